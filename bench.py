@@ -1,0 +1,381 @@
+"""Benchmark: batched multi-scale range-image registration on one B300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--pairs B] [--impl ours|reference]
+
+A step registers B pairs of 64 x 1024 float32 range images (HDL-64-like
+elevation table, seeded 200-object outdoor scenes) with 4 pyramid levels x 10
+Gauss-Newton iterations: target normals + plane pyramid, source pyramid and
+40 fused association/reduction/solve launches, all in librimg.  One JSON line
+is printed by rank 0.  Under torchrun each rank registers its own B pairs
+(weak scaling, no data-path collective); the step time is the max over ranks.
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload on the host cores (the oracle is the only reference that exists).
+"""
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "64x1024 scan-pair registrations/sec on 1 B300 at ≤1e-4 rad/m pose error; HBM GB/s"
+WORKLOAD = "pair64x1024"
+BYTES_PER_SRC_PIXEL = 20      # 4 B source range + 16 B target plane (n, d) per source pixel per iteration
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--pairs", type=int, default=512, help="pairs per step per GPU")
+    ap.add_argument("--unique", type=int, default=128, help="distinct seeded pairs generated per GPU")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-pairs", type=int, default=8)
+    ap.add_argument("--e2e-chunk", type=int, default=128)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def shard_seed_offset(rank, pairs_per_rank):
+    """Each rank registers its own disjoint range of seeded pair indices."""
+    return rank * pairs_per_rank
+
+
+def workload_config(args, unique):
+    from synth import CONFIGS
+    cfg = CONFIGS[WORKLOAD]
+    return cfg, {
+        "workload": f"{WORKLOAD}: {cfg.H}x{cfg.W} float32 range-image pairs, HDL-64-like elevation table, "
+                    f"{cfg.n_objects}-object seeded outdoor scenes, rot<={cfg.rot_max_deg}deg "
+                    f"trans<={cfg.trans_max}m, sigma {cfg.sigma} m, {int(cfg.dropout * 100)}% invalid; "
+                    f"{cfg.levels} levels x {list(cfg.iters)} Gauss-Newton iterations",
+        "pairs_per_step_per_gpu": args.pairs,
+        "unique_pairs_per_gpu": unique,
+        "levels": cfg.levels,
+        "iters_coarse_to_fine": list(cfg.iters),
+        "huber_delta_m": cfg.huber_delta,
+        "l2": "inputs larger than L2 (source+target ranges %.0f MB, target planes %.0f MB per step)" % (
+            args.pairs * cfg.H * cfg.W * 8 / 1e6, args.pairs * cfg.H * cfg.W * 16 * 4 / 3 / 1e6),
+        "parallelism": "replicas by pair (weak scaling)",
+    }
+
+
+def gen_pairs(cfg, start, unique, total):
+    """`unique` seeded pairs, tiled to `total` (each copy in its own buffer)."""
+    from synth import make_pairs
+    procs = max(1, min(32, (os.cpu_count() or 2) - 1))
+    src, dst, Tgt = make_pairs(cfg, range(start, start + unique), processes=procs)
+    reps = -(-total // unique)
+    return (np.ascontiguousarray(np.tile(src, (reps, 1, 1))[:total]),
+            np.ascontiguousarray(np.tile(dst, (reps, 1, 1))[:total]),
+            np.tile(Tgt, (reps, 1, 1))[:total])
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("kernel_icp.cu", "rimg_device.cuh", "rimg_internal.h"):
+        with open(os.path.join(ROOT, "paper_2112_02779_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(pairs):
+    """DRAM bytes per level-0 icp_step launch from the committed ncu summary,
+    scaled to `pairs` pairs; None when absent or taken on another kernel
+    version."""
+    path = os.path.join(ROOT, "profiles", "icp_step_level0_64x1024.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m_hash = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", txt)
+    m_b = re.search(r"dram_bytes_per_pair_per_launch:\s*([0-9.eE+]+)", txt)
+    if not m_hash or not m_b or m_hash.group(1) != kernel_source_hash():
+        return None
+    return float(m_b.group(1)) * pairs
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def cpu_oracle_sample(cfg, src, dst, n):
+    """Time the FP64 oracle registering n pairs on one host thread."""
+    from oracle import rimg_oracle as O
+    try:
+        from threadpoolctl import threadpool_limits
+        ctx = threadpool_limits(1)
+    except Exception:                       # pragma: no cover
+        import contextlib
+        ctx = contextlib.nullcontext()
+    s = cfg.sensor()
+    sens = (s.phi_lut, s.theta_lut, s.r0)
+    params = dict(huber_delta=float(np.float32(cfg.huber_delta)), max_corr_dist=0.0,
+                  normal_rel_jump=float(np.float32(0.1)))
+    poses = []
+    with ctx:
+        t0 = time.perf_counter()
+        for i in range(n):
+            T, _ = O.register(src[i], dst[i], sens, sens, np.eye(4), cfg.levels, cfg.iters, params)
+            poses.append(T)
+        dt = time.perf_counter() - t0
+    return n / dt, dt, poses
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    args.pairs = 1
+    cfg, config = workload_config(args, unique=1)
+    from synth import make_pair
+    p = make_pair(cfg, 0)
+    src, dst = p["src_range"][None], p["dst_range"][None]
+    for _ in range(args.warmup):
+        cpu_oracle_sample(cfg, src, dst, 1)
+    times = []
+    for _ in range(args.steps):
+        _, dt, _ = cpu_oracle_sample(cfg, src, dst, 1)
+        times.append(dt)
+    total = sum(times)
+    value = args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded ray-cast scenes)", "config": config,
+        "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": 1, "kind": "oracle",
+                         "sample": "1 pair of the workload per step, FP64 numpy oracle, one host thread"},
+        "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    rank, world, local = dist_env()
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    cfg, config = workload_config(args, min(args.unique, args.pairs))
+    B = args.pairs
+    unique = min(args.unique, B)
+    # host data first: the generator pool is spawned before any CUDA call
+    src_np, dst_np, Tgt = gen_pairs(cfg, shard_seed_offset(rank, unique), unique, B)
+    torch.cuda.set_device(local)
+    import paper_2112_02779_b300.rimg as R   # raises if librimg.so is missing
+    dev = torch.device("cuda", local)
+    s = cfg.sensor()
+    sens = R.rimg_sensor_build(cfg.H, cfg.W, cfg.levels, s.phi_lut, s.theta_lut, s.r0)
+    params = R.rimg_default_params(huber_delta=cfg.huber_delta)
+    src = torch.from_numpy(src_np).to(dev)
+    dst = torch.from_numpy(dst_np).to(dev)
+    T0 = torch.eye(4, dtype=torch.float64, device=dev).reshape(1, 16).repeat(B, 1).contiguous()
+    T1 = torch.empty_like(T0)
+    status = torch.empty(B, dtype=torch.int32, device=dev)
+    ws = torch.empty(R.rimg_register_workspace_bytes(sens, sens, B, cfg.levels), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        R.rimg_register(sens, sens, B, src, dst, T0, T1, cfg.levels, cfg.iters, params, status, ws, stream)
+
+    warmup = max(args.warmup, 3)          # at least three untimed steps
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize(dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    launches_per_step = 2 + sum(cfg.iters)
+    R.rimg_profile_begin(launches_per_step * args.steps + 16)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize(dev)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+    recs = R.rimg_profile_end()
+    ms_total = ev0.elapsed_time(ev1)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms_total], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    value = world * B * args.steps / (ms_total / 1e3)
+
+    # per-kernel launch durations from the library's own event pairs
+    per = {}
+    for kid, lvl, npairs, ms in recs:
+        key = (R.KERNEL_NAMES[kid], lvl)
+        per.setdefault(key, []).append(ms)
+    N0 = cfg.H * cfg.W
+    l0 = per.get(("icp_step", 0), [float("nan")])
+    l0_ms = float(np.mean(l0))
+    algo_bytes = B * N0 * BYTES_PER_SRC_PIXEL
+    achieved = algo_bytes / (l0_ms / 1e3) / 1e9
+    peak, peak_kind = measured_peak()
+    traffic = recorded_traffic(B)
+    icp_total = sum(sum(v) for k, v in per.items() if k[0] == "icp_step")
+    all_total = sum(sum(v) for v in per.values())
+
+    torch.cuda.synchronize(dev)
+    Tg = T1.cpu().numpy().reshape(B, 4, 4)
+    st = status.cpu().numpy()
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    hs = torch.from_numpy(src_np).pin_memory()
+    hd = torch.from_numpy(dst_np).pin_memory()
+    hT0 = torch.eye(4, dtype=torch.float64).reshape(1, 16).repeat(B, 1).contiguous().pin_memory()
+    hT1 = torch.zeros((B, 16), dtype=torch.float64).pin_memory()
+    hst = torch.zeros(B, dtype=torch.int32).pin_memory()
+    chunk = min(args.e2e_chunk, B)
+    ws_h = torch.empty(R.rimg_register_host_workspace_bytes(sens, sens, B, cfg.levels, chunk), dtype=torch.uint8,
+                       device=dev)
+    del ws
+    for _ in range(2):
+        R.rimg_register_host(sens, sens, B, hs, hd, hT0, hT1, cfg.levels, cfg.iters, params, hst, chunk, ws_h,
+                             stream)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        R.rimg_register_host(sens, sens, B, hs, hd, hT0, hT1, cfg.levels, cfg.iters, params, hst, chunk, ws_h,
+                             stream)
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_s], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+        barrier()
+    e2e_value = world * B * args.steps / e2e_s
+    e2e_same = bool(np.array_equal(hT1.numpy().reshape(B, 4, 4), Tg))
+
+    if rank != 0:
+        return 0
+    line = {
+        "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
+        "warmup": warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded ray-cast scenes)", "config": config,
+        "roofline": {"bound": "hbm", "kernel": "icp_step (level 0, 64x1024)", "achieved": achieved,
+                     "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": peak_kind, "algorithmic_bytes_per_launch": algo_bytes,
+                     "avg_launch_ms": l0_ms, "launches": len(l0)},
+        "kernels": {f"{k[0]}@L{k[1]}": {"launches": len(v), "avg_ms": float(np.mean(v)),
+                                        "share": float(sum(v) / all_total)} for k, v in sorted(per.items())},
+        "icp_share_of_kernel_time": icp_total / all_total if all_total else None,
+        "e2e": {"value": e2e_value, "unit": "pairs/s",
+                "h2d_bytes_per_step": int(B * N0 * 4 * 2 + B * 16 * 8),
+                "d2h_bytes_per_step": int(B * 16 * 8 + B * 4), "chunk_pairs": chunk,
+                "poses_equal_device_path": e2e_same},
+        "gpu_launches": len(recs),
+        "clocks": clk.summary(),
+        "degenerate_pairs": int(np.sum(st & 1)),
+        "pose_err_vs_ground_truth_median": None,
+    }
+    from oracle import rimg_oracle as O  # used only for the metric below and the CPU baseline leg
+    errs = [O.pose_error(Tg[i], Tgt[i]) for i in range(min(B, unique))]
+    line["pose_err_vs_ground_truth_median"] = {"rot_rad": float(np.median([e[0] for e in errs])),
+                                               "trans_m": float(np.median([e[1] for e in errs]))}
+    if not args.no_cpu_baseline and world == 1:
+        n = min(args.cpu_sample_pairs, unique)
+        v, dt, poses = cpu_oracle_sample(cfg, src_np, dst_np, n)
+        pe = [O.pose_error(Tg[i], poses[i]) for i in range(n)]
+        line["cpu_baseline"] = {"value": v, "unit": "pairs/s", "cores": 1, "kind": "oracle",
+                                "sample": f"{n} pairs of the workload, FP64 numpy oracle, one host thread, "
+                                          f"{dt:.1f} s",
+                                "pose_err_gpu_vs_oracle_max": {"rot_rad": max(e[0] for e in pe),
+                                                               "trans_m": max(e[1] for e in pe)}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

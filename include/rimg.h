@@ -1,0 +1,257 @@
+/*
+ * rimg.h -- C ABI of the B300 range-image registration library (librimg.so).
+ *
+ * The library registers LiDAR scans stored as cylindrical range images by
+ * multi-scale projective point-to-plane Gauss-Newton, the method of
+ * "Revisiting LiDAR Registration and Reconstruction: A Range Image
+ * Perspective" (arXiv 2112.02779), Sections 3 and 4.1.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Images are float32, row-major [H][W]; row v is the beam (elevation)
+ *    index, column u the azimuth index (Section 3).  Batches of images are
+ *    stacked as [n][H][W].  A range <= 0 or not finite marks an invalid pixel.
+ *  - All image, table, pose and workspace pointers are DEVICE pointers owned
+ *    by the caller, except where a parameter says "host".  The library never
+ *    allocates device memory (entry points that need scratch take a caller
+ *    workspace whose size is returned by the matching *_workspace_bytes call).
+ *  - Poses are float64 row-major 4x4 matrices T that map source-frame points
+ *    into the target frame, x = R p + t (Eq. 5).
+ *  - Every call is asynchronous on `stream` (a cudaStream_t; NULL = the legacy
+ *    default stream) unless stated otherwise.  Calls return RIMG_OK (0) or a
+ *    negative rimg_status; nothing is thrown across the ABI.  On an error no
+ *    kernel has been launched unless the code is RIMG_ERR_CUDA.
+ *  - Thread safety: calls may be made from several host threads on different
+ *    streams if they use different workspaces.
+ */
+#ifndef RIMG_H
+#define RIMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RIMG_MAX_LEVELS 8
+
+typedef enum rimg_status {
+  RIMG_OK = 0,
+  RIMG_ERR_INVALID_ARG = -1,      /* null pointer, negative count, bad parameter */
+  RIMG_ERR_LUT = -2,              /* elevation table not strictly monotone / out of range */
+  RIMG_ERR_SIZE = -3,             /* image size incompatible with the pyramid (see rimg_sensor_build) */
+  RIMG_ERR_WORKSPACE = -4,        /* workspace too small or not 256-byte aligned */
+  RIMG_ERR_CUDA = -5,             /* a CUDA runtime call failed; see rimg_last_error() */
+  RIMG_ERR_MISMATCH = -6          /* source and target sensors disagree where they must agree */
+} rimg_status;
+
+/* Per-pair status bits written by rimg_icp_step / rimg_register. */
+#define RIMG_FLAG_DEGENERATE 1    /* an iteration had < 6 correspondences or a Cholesky pivot
+                                     <= 1e-12 * trace(J^T W J); its update was skipped */
+
+/* One pyramid level of a sensor's device tables (filled by rimg_sensor_build;
+ * callers treat it as read-only). */
+typedef struct rimg_level {
+  int H, W;                 /* level size: H >> l, W >> l */
+  int n_bins;               /* entries of the inverse elevation table */
+  int tie_up;               /* 1 when elevation decreases with the row index */
+  float s_lo, s_hi;         /* vertical field of view as sin(elevation) */
+  float bin_scale;          /* n_bins / (s_hi - s_lo) */
+  float w_over_2pi;         /* W / (2 pi) */
+  size_t off_rows;          /* float4[H]: cos phi, sin phi, cos theta_lut, sin theta_lut */
+  size_t off_cols;          /* float2[W]: cos, sin of the column angle 2 pi u / W */
+  size_t off_thu;           /* float[H]:  theta_lut[v] * W / (2 pi) */
+  size_t off_rank;          /* int[H]:    row of the j-th smallest elevation */
+  size_t off_bnd;           /* float[H-1]: sin of the mid-elevation between ranks j, j+1 */
+  size_t off_bins;          /* int[n_bins]: rank at each bin's lower edge */
+} rimg_level;
+
+/* A sensor's intrinsics in device form: the elevation table phi_lut and the
+ * azimuth-offset table theta_lut of Section 3 (Eq. 1-2), the receiver radius
+ * r0, and per-level tables for the strided pyramid of Section 4.1. */
+typedef struct rimg_sensor {
+  int H, W, levels;
+  float r0;
+  void* d_tables;           /* device, caller-owned, rimg_sensor_table_bytes() long */
+  size_t table_bytes;
+  rimg_level level[RIMG_MAX_LEVELS];
+} rimg_sensor;
+
+/* Method parameters.  Defaults (rimg_default_params): huber_delta 0.5 m (the
+ * outdoor kernel size of Section 6.1), no distance gate, normal_rel_jump 0.1,
+ * proj_iters 3, kahan 1. */
+typedef struct rimg_params {
+  float huber_delta;        /* pseudo-Huber kernel size (m); <= 0: plain least squares */
+  float max_corr_dist;      /* reject pairs with |x - q| > max_corr_dist; <= 0: off */
+  float normal_rel_jump;    /* a normal needs |r_nb - r_c| <= normal_rel_jump * r_c, in [0, 0.5) */
+  int proj_iters;           /* receiver-offset fixed-point steps when r0 != 0 (1..16) */
+  int kahan;                /* 1: Kahan-compensated FP32 accumulation of J^T W J / J^T W e */
+} rimg_params;
+
+/* Fill *p with the defaults above.  Host only. */
+int rimg_default_params(rimg_params* p);
+
+/* Human-readable text of a status code; never NULL. */
+const char* rimg_status_string(int code);
+
+/* Text of the last RIMG_ERR_CUDA (per host thread); "" if none. */
+const char* rimg_last_error(void);
+
+/* ---------------------------------------------------------------------------
+ * Sensor tables (step A1: host, once per sensor).
+ *
+ * Section 3.1-3.2: the elevation table phi_lut[H] and azimuth offsets
+ * theta_lut[H] (radians, HOST float64 arrays) come from the manufacturer.
+ * The library precomputes, per pyramid level l (rows 2^l v of the finest
+ * tables, W_l = W >> l), separable cos/sin tables for Eq. 1 and an inverse
+ * elevation table (the 2H-entry table of Section 3.2, refined to the exact
+ * Eq. 4 argmin by walking row boundaries).
+ *
+ * Requirements: levels in [1, RIMG_MAX_LEVELS]; H >> (levels-1) >= 2;
+ * W divisible by 4 << (levels-1); phi_lut finite, strictly monotone, inside
+ * (-pi/2, pi/2); |theta_lut| < pi; r0 finite and >= 0.  Otherwise
+ * RIMG_ERR_SIZE / RIMG_ERR_LUT / RIMG_ERR_INVALID_ARG.
+ *
+ * rimg_sensor_build copies the tables into d_tables SYNCHRONOUSLY (blocking
+ * cudaMemcpy) and fills *out; it is not meant for the hot path.
+ * ------------------------------------------------------------------------- */
+int rimg_sensor_table_bytes(int H, int W, int levels, size_t* bytes);
+int rimg_sensor_build(int H, int W, int levels, const double* phi_lut, const double* theta_lut,
+                      double r0, void* d_tables, size_t table_bytes, rimg_sensor* out);
+
+/* ---------------------------------------------------------------------------
+ * Unprojection Pi^-1 (step A2), Eq. 1-2: for each pixel of level `level` of
+ * n_images range images range[n][H_l][W_l],
+ *   x = r cos(theta) cos(phi) + r0 cos(2 pi u / W_l)
+ *   y = r sin(theta) cos(phi) + r0 sin(2 pi u / W_l)
+ *   z = r sin(phi),  theta = 2 pi u / W_l + theta_lut[v], phi = phi_lut[v]
+ * xyz: float32 [n][3][H_l][W_l] (three planes); invalid pixels get the point of
+ * r = 0.  mask (nullable): uint8 [n][H_l][W_l], 1 = valid range.
+ * ------------------------------------------------------------------------- */
+int rimg_unproject(const rimg_sensor* s, int level, int n_images, const float* range,
+                   float* xyz, uint8_t* mask, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Pyramid (step A3), Section 4.1: level l is the finest image strided by 2^l
+ * in rows and columns, Omega_l(u, v) = Omega_0(2^l u, 2^l v) (an exact copy;
+ * intrinsics stay those of the finest level).
+ * in: [n][H][W][channels] float32 with channels 1 (ranges) or 4 (planes);
+ * out_levels: HOST array of `levels` device pointers; entry l (l >= 1) receives
+ * [n][H >> l][W >> l][channels]; entry 0 is ignored (level 0 is `in`).
+ * H and W must be divisible by 2^(levels-1).
+ * ------------------------------------------------------------------------- */
+int rimg_pyramid(int n_images, int H, int W, int levels, int channels, const float* in,
+                 float* const* out_levels, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Normals (step A4), Section 4.1 ("cross product of two neighbor pixels"):
+ * at finest-level pixel (u, v) with points P from Eq. 1,
+ *   a = P(u+1, v) - P(u-1, v)   (u wraps around the 360 degree image)
+ *   b = P(u, v+1) - P(u, v-1)
+ *   n = a x b / |a x b|, flipped so that n . P(u, v) <= 0 (facing the sensor).
+ * Invalid (plane = 0) on rows 0 and H-1, when any of the five ranges is invalid,
+ * when |r_nb - r_c| > normal_rel_jump * r_c for a neighbour (decided exactly),
+ * or when |a x b| <= 1e-4 |a| |b|.
+ * Output is a plane image per level: planes_levels (HOST array of s->levels
+ * device pointers) entry l receives float4 [n][H_l][W_l] = (n_x, n_y, n_z, d)
+ * with d = n . P, strided from the finest level like rimg_pyramid (normals are
+ * strided, not recomputed, Section 4.1).  mask0 (nullable): uint8 [n][H][W],
+ * 1 = valid normal at the finest level.
+ * ------------------------------------------------------------------------- */
+int rimg_normals(const rimg_sensor* s, int n_images, const float* range, const rimg_params* p,
+                 float* const* planes_levels, uint8_t* mask0, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * One projective-association Gauss-Newton step (steps A5-A8), Section 4.1,
+ * Eq. 5-7, for n_pairs independent pairs at pyramid level `level`.
+ *
+ * For every source pixel i of level l (src_range_l [n][H_l][W_l] of sensor
+ * `src`): p = Pi^-1(u, v, r) (Eq. 1), x = R p + t with T = pose[pair]; the
+ * target pixel (u', v') = Pi(x) at level l of sensor `dst` (Eq. 3-4 with the
+ * receiver-offset fixed point, rows by the exact Eq. 4 argmin, columns
+ * rounded half up and wrapped); the pair is valid when the source range is
+ * valid, the elevation lies within half an edge-row spacing of the table,
+ * the target plane (n, d) at (u', v') is valid and, if max_corr_dist > 0,
+ * |x - q| <= max_corr_dist.  Then e = n . x - d (= n^T (x - q)), weight
+ * w = 1/sqrt(1 + (e/delta)^2) (pseudo-Huber IRLS), J = [x cross n, n] for the
+ * left perturbation x <- Exp(xi) x, and the library reduces
+ *   J^T W J (21 upper-triangle terms, row-major), J^T W e (6), sum w e^2, count
+ * (29 values, FP32 per thread with optional Kahan compensation, FP64 across
+ * blocks).  With `update` != 0 it solves (J^T W J) xi = -J^T W e by an FP64
+ * Cholesky factorisation and sets T <- Exp(xi) T in place; a degenerate system
+ * (count < 6 or pivot <= 1e-12 trace) leaves T unchanged and sets
+ * RIMG_FLAG_DEGENERATE in status[pair] (status is OR-ed, never cleared here).
+ *
+ * dst_planes_l: float4 [n][H_l][W_l] from rimg_normals; dst_range_l
+ * ([n][H_l][W_l]) is read only when max_corr_dist > 0 (may be NULL otherwise).
+ * pose: float64 [n][16] device.  out29 (nullable): float64 [n][29] device.
+ * assoc (nullable): int32 [n][H_l][W_l] device, v' * W_l + u' or -1.
+ * status (nullable): int32 [n] device.  Source and target must have the same
+ * number of levels (RIMG_ERR_MISMATCH otherwise).
+ * workspace: device, 256-byte aligned, >= rimg_icp_workspace_bytes(); its
+ * first bytes hold per-pair counters that every call leaves at zero (the call
+ * zeroes them with cudaMemsetAsync before its kernel).
+ * ------------------------------------------------------------------------- */
+int rimg_icp_workspace_bytes(const rimg_sensor* src, int n_pairs, size_t* bytes);
+int rimg_icp_step(const rimg_sensor* src, const rimg_sensor* dst, int level, int n_pairs,
+                  const float* src_range_l, const float* dst_planes_l, const float* dst_range_l,
+                  double* pose, const rimg_params* p, int update, double* out29, int32_t* assoc,
+                  int* status, void* workspace, size_t workspace_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Multi-scale registration (step A9), Section 4.1 with the coarse-to-fine
+ * schedule of Section 6.1: normals of every target at the finest level, the
+ * strided source-range and target-plane pyramids, then for each level from the
+ * coarsest (levels-1) to the finest (0) iters[k] Gauss-Newton steps
+ * (iters is a HOST array listed coarse -> fine); the pose carries over between
+ * levels unchanged.  All n_pairs pairs share the two sensors and are
+ * registered together (one kernel per step covers every pair).
+ *
+ * src_range, dst_range: float32 [n][H][W] device.  T_init, T_out: float64
+ * [n][16] device (they may alias).  status (nullable): int32 [n] device, set
+ * to 0 and then OR-ed with RIMG_FLAG_* bits.  workspace: device, 256-byte
+ * aligned, >= rimg_register_workspace_bytes().  1 <= levels <= each sensor's
+ * levels; both sensors must agree on H, W.
+ * ------------------------------------------------------------------------- */
+int rimg_register_workspace_bytes(const rimg_sensor* src, const rimg_sensor* dst, int n_pairs,
+                                  int levels, size_t* bytes);
+int rimg_register(const rimg_sensor* src, const rimg_sensor* dst, int n_pairs,
+                  const float* src_range, const float* dst_range, const double* T_init,
+                  double* T_out, int levels, const int* iters, const rimg_params* p, int* status,
+                  void* workspace, size_t workspace_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * rimg_register with HOST inputs and outputs: copies src_range/dst_range
+ * ([n][H][W] float32) and T_init ([n][16] float64) from host memory (pinned
+ * memory overlaps best) into the workspace, registers, copies T_out (host,
+ * [n][16]) and status (host int32 [n], nullable) back, and SYNCHRONISES the
+ * stream before returning.  workspace >= rimg_register_host_workspace_bytes().
+ * The transfer is split into chunks of pairs on `stream` so that the copy of
+ * one chunk overlaps the registration of the previous one when
+ * chunk_pairs < n_pairs (chunk_pairs <= 0: one chunk).
+ * ------------------------------------------------------------------------- */
+int rimg_register_host_workspace_bytes(const rimg_sensor* src, const rimg_sensor* dst,
+                                       int n_pairs, int levels, int chunk_pairs, size_t* bytes);
+int rimg_register_host(const rimg_sensor* src, const rimg_sensor* dst, int n_pairs,
+                       const float* src_range_host, const float* dst_range_host,
+                       const double* T_init_host, double* T_out_host, int levels, const int* iters,
+                       const rimg_params* p, int* status_host, int chunk_pairs, void* workspace,
+                       size_t workspace_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Launch timing (tracing).  rimg_profile_begin(max) makes subsequent library
+ * launches on any stream record a CUDA event pair around each kernel (at most
+ * `max` launches; later ones are not recorded).  rimg_profile_end waits for
+ * the recorded events, writes up to `cap` records (kernel id, level, n_pairs,
+ * milliseconds) and stops recording; it returns the number of records.
+ * Kernel ids: 0 unproject, 1 pyramid, 2 normals (+ plane pyramid),
+ * 3 icp step, 4 source-range pyramid.  Not for use during stream capture.
+ * ------------------------------------------------------------------------- */
+int rimg_profile_begin(int max_launches);
+int rimg_profile_end(int cap, int* kernel_id, int* level, int* n_pairs, float* ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RIMG_H */

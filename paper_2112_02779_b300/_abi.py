@@ -1,0 +1,38 @@
+"""ctypes mirrors of the structs in include/rimg.h (layout checked by a test
+that compiles the header with gcc)."""
+import ctypes
+
+RIMG_MAX_LEVELS = 8
+RIMG_FLAG_DEGENERATE = 1
+
+STATUS_NAMES = {0: "RIMG_OK", -1: "RIMG_ERR_INVALID_ARG", -2: "RIMG_ERR_LUT", -3: "RIMG_ERR_SIZE",
+                -4: "RIMG_ERR_WORKSPACE", -5: "RIMG_ERR_CUDA", -6: "RIMG_ERR_MISMATCH"}
+
+
+class rimg_level(ctypes.Structure):
+    _fields_ = [("H", ctypes.c_int), ("W", ctypes.c_int), ("n_bins", ctypes.c_int), ("tie_up", ctypes.c_int),
+                ("s_lo", ctypes.c_float), ("s_hi", ctypes.c_float), ("bin_scale", ctypes.c_float),
+                ("w_over_2pi", ctypes.c_float),
+                ("off_rows", ctypes.c_size_t), ("off_cols", ctypes.c_size_t), ("off_thu", ctypes.c_size_t),
+                ("off_rank", ctypes.c_size_t), ("off_bnd", ctypes.c_size_t), ("off_bins", ctypes.c_size_t)]
+
+
+class rimg_sensor(ctypes.Structure):
+    _fields_ = [("H", ctypes.c_int), ("W", ctypes.c_int), ("levels", ctypes.c_int), ("r0", ctypes.c_float),
+                ("d_tables", ctypes.c_void_p), ("table_bytes", ctypes.c_size_t),
+                ("level", rimg_level * RIMG_MAX_LEVELS)]
+
+
+class rimg_params(ctypes.Structure):
+    _fields_ = [("huber_delta", ctypes.c_float), ("max_corr_dist", ctypes.c_float),
+                ("normal_rel_jump", ctypes.c_float), ("proj_iters", ctypes.c_int), ("kahan", ctypes.c_int)]
+
+
+# Every function include/rimg.h declares (checked against the header and the
+# library's exports by the CPU test-suite).
+HEADER_FUNCTIONS = [
+    "rimg_default_params", "rimg_status_string", "rimg_last_error",
+    "rimg_sensor_table_bytes", "rimg_sensor_build", "rimg_unproject", "rimg_pyramid", "rimg_normals",
+    "rimg_icp_workspace_bytes", "rimg_icp_step", "rimg_register_workspace_bytes", "rimg_register",
+    "rimg_register_host_workspace_bytes", "rimg_register_host", "rimg_profile_begin", "rimg_profile_end",
+]

@@ -1,0 +1,187 @@
+// Per-image preprocessing kernels: unprojection (Eq. 1-2), the strided
+// pyramid (Section 4.1) and neighbour-cross-product normals (Section 4.1)
+// with the target plane pyramid written by the same kernel.
+#include "rimg_device.cuh"
+
+namespace rimg {
+
+// --------------------------------------------------------------------------
+// Unprojection: one thread per pixel, three coalesced output planes.
+__global__ void __launch_bounds__(256) k_unproject(DevLevel L, int n, const float* __restrict__ range,
+                                                   float* __restrict__ xyz, uint8_t* __restrict__ mask) {
+  const long long N = (long long)L.H * L.W;
+  const long long total = N * n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long img = i / N;
+    const int pix = (int)(i - img * N);
+    const int v = pix / L.W, u = pix - v * L.W;
+    const float r = __ldcs(range + i);
+    const bool ok = range_ok(r);
+    const float3 p = unproject_px(L, u, v, ok ? r : 0.f);
+    float* base = xyz + img * 3 * N + pix;
+    __stcs(base, p.x);
+    __stcs(base + N, p.y);
+    __stcs(base + 2 * N, p.z);
+    if (mask) mask[i] = ok ? 1 : 0;
+  }
+}
+
+cudaError_t launch_unproject(const DevLevel& L, int n, const float* range, float* xyz,
+                             uint8_t* mask, cudaStream_t st) {
+  const long long total = (long long)L.H * L.W * n;
+  if (total == 0) return cudaSuccess;
+  const int threads = 256;
+  long long blocks = (total + threads - 1) / threads;
+  if (blocks > 148LL * 64) blocks = 148LL * 64;
+  k_unproject<<<(unsigned)blocks, threads, 0, st>>>(L, n, range, xyz, mask);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// Strided pyramid: one thread per level-1 pixel; it copies Omega_0(2u, 2v) to
+// level 1 and, where its level-1 coordinates are even, to the coarser levels.
+template <typename T>
+struct PyrOut {
+  T* p[RIMG_MAX_LEVELS];
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_pyramid(int n, int H, int W, int levels, const T* __restrict__ in,
+                                                 PyrOut<T> out) {
+  const int H1 = H >> 1, W1 = W >> 1;
+  const long long N1 = (long long)H1 * W1;
+  const long long total = N1 * n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long img = i / N1;
+    const int pix = (int)(i - img * N1);
+    const int v1 = pix / W1, u1 = pix - v1 * W1;
+    const T val = in[img * (long long)H * W + (long long)(2 * v1) * W + 2 * u1];
+    out.p[1][i] = val;
+    for (int l = 2; l < levels; ++l) {
+      const int m = (1 << (l - 1)) - 1;
+      if ((u1 & m) | (v1 & m)) break;
+      const int Hl = H >> l, Wl = W >> l;
+      out.p[l][img * (long long)Hl * Wl + (long long)(v1 >> (l - 1)) * Wl + (u1 >> (l - 1))] = val;
+    }
+  }
+}
+
+cudaError_t launch_pyramid(int n, int H, int W, int levels, int channels, const float* in,
+                           float* const* out_levels, cudaStream_t st) {
+  if (levels < 2 || n == 0) return cudaSuccess;
+  const long long total = (long long)(H >> 1) * (W >> 1) * n;
+  const int threads = 256;
+  long long blocks = (total + threads - 1) / threads;
+  if (blocks > 148LL * 64) blocks = 148LL * 64;
+  if (channels == 1) {
+    PyrOut<float> o{};
+    for (int l = 1; l < levels; ++l) o.p[l] = out_levels[l];
+    k_pyramid<float><<<(unsigned)blocks, threads, 0, st>>>(n, H, W, levels, in, o);
+  } else {
+    PyrOut<float4> o{};
+    for (int l = 1; l < levels; ++l) o.p[l] = reinterpret_cast<float4*>(out_levels[l]);
+    k_pyramid<float4><<<(unsigned)blocks, threads, 0, st>>>(n, H, W, levels,
+                                                            reinterpret_cast<const float4*>(in), o);
+  }
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// Normals.  A 32 x 8 tile of output pixels per block; the block unprojects the
+// (32+2) x (8+2) halo tile into shared memory once (u wraps, rows outside the
+// image are invalid), then each thread forms the two central differences,
+// their cross product and the validity tests, and writes the plane
+// (n, n . P) to level 0 and, when its coordinates are multiples of 2^l, to
+// level l (the strided normal pyramid).
+constexpr int NT_X = 32, NT_Y = 8;
+constexpr int NH_X = NT_X + 2, NH_Y = NT_Y + 2;
+
+struct PlaneOut {
+  float4* p[RIMG_MAX_LEVELS];
+};
+
+__global__ void __launch_bounds__(NT_X* NT_Y) k_normals(DevLevel L, int levels, int n, const float* __restrict__ range,
+                                                        float rel_jump, PlaneOut out,
+                                                        uint8_t* __restrict__ mask0) {
+  __shared__ float sx[NH_Y][NH_X], sy[NH_Y][NH_X], sz[NH_Y][NH_X], sr[NH_Y][NH_X];
+  const int img = blockIdx.z;
+  const int u0 = blockIdx.x * NT_X - 1, v0 = blockIdx.y * NT_Y - 1;
+  const int H = L.H, W = L.W;
+  const float* rimg = range + (long long)img * H * W;
+  const int tid = threadIdx.y * NT_X + threadIdx.x;
+  for (int k = tid; k < NH_X * NH_Y; k += NT_X * NT_Y) {
+    const int hy = k / NH_X, hx = k - hy * NH_X;
+    const int v = v0 + hy;
+    int u = (u0 + hx) % W;          // the halo wraps around the 360 degree image
+    u = (u < 0) ? u + W : u;
+    float r = 0.f;
+    if (v >= 0 && v < H) r = __ldg(rimg + (long long)v * W + u);
+    const bool ok = (v >= 0 && v < H) && range_ok(r);
+    float3 p = make_float3(0.f, 0.f, 0.f);
+    if (ok) p = unproject_px(L, u, v, r);
+    sx[hy][hx] = p.x;
+    sy[hy][hx] = p.y;
+    sz[hy][hx] = p.z;
+    sr[hy][hx] = ok ? r : 0.f;   // 0 marks an invalid pixel
+  }
+  __syncthreads();
+  const int u = blockIdx.x * NT_X + threadIdx.x;
+  const int v = blockIdx.y * NT_Y + threadIdx.y;
+  if (u >= W || v >= H) return;
+  const int cx = threadIdx.x + 1, cy = threadIdx.y + 1;
+  const float rc = sr[cy][cx];
+  const float rl = sr[cy][cx - 1], rr = sr[cy][cx + 1], ru = sr[cy - 1][cx], rd = sr[cy + 1][cx];
+  // |r_nb - r_c| <= rel_jump * r_c decided exactly: the difference is exact
+  // (Sterbenz) whenever the test can pass, and the sign of one fused
+  // multiply-add is the sign of the exact value.
+  bool ok = (v > 0) && (v < H - 1) && rc > 0.f && rl > 0.f && rr > 0.f && ru > 0.f && rd > 0.f;
+  ok = ok && fmaf(rel_jump, rc, -fabsf(rl - rc)) >= 0.f && fmaf(rel_jump, rc, -fabsf(rr - rc)) >= 0.f &&
+       fmaf(rel_jump, rc, -fabsf(ru - rc)) >= 0.f && fmaf(rel_jump, rc, -fabsf(rd - rc)) >= 0.f;
+  const float ax = sx[cy][cx + 1] - sx[cy][cx - 1], ay = sy[cy][cx + 1] - sy[cy][cx - 1],
+              az = sz[cy][cx + 1] - sz[cy][cx - 1];
+  const float bx = sx[cy + 1][cx] - sx[cy - 1][cx], by = sy[cy + 1][cx] - sy[cy - 1][cx],
+              bz = sz[cy + 1][cx] - sz[cy - 1][cx];
+  float nx = fmaf(ay, bz, -az * by), ny = fmaf(az, bx, -ax * bz), nz = fmaf(ax, by, -ay * bx);
+  const float c2 = fmaf(nx, nx, fmaf(ny, ny, nz * nz));
+  const float a2 = fmaf(ax, ax, fmaf(ay, ay, az * az));
+  const float b2 = fmaf(bx, bx, fmaf(by, by, bz * bz));
+  ok = ok && (c2 > 1e-8f * a2 * b2);
+  float4 plane = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (ok) {
+    const float inv = rsqrtf(c2);
+    nx *= inv; ny *= inv; nz *= inv;
+    const float px = sx[cy][cx], py = sy[cy][cx], pz = sz[cy][cx];
+    float d = fmaf(nx, px, fmaf(ny, py, nz * pz));
+    if (d > 0.f) { nx = -nx; ny = -ny; nz = -nz; d = -d; }
+    plane = make_float4(nx, ny, nz, d);
+  }
+  const long long N = (long long)H * W;
+  out.p[0][img * N + (long long)v * W + u] = plane;
+  if (mask0) mask0[img * N + (long long)v * W + u] = ok ? 1 : 0;
+  for (int l = 1; l < levels; ++l) {
+    const int m = (1 << l) - 1;
+    if ((u & m) | (v & m)) break;
+    const int Hl = H >> l, Wl = W >> l;
+    out.p[l][img * (long long)Hl * Wl + (long long)(v >> l) * Wl + (u >> l)] = plane;
+  }
+}
+
+cudaError_t launch_normals(const rimg_sensor* s, int n, const float* range, float rel_jump,
+                           float* const* planes_levels, uint8_t* mask0, cudaStream_t st) {
+  const DevLevel L = dev_level(s, 0);
+  const long long N = (long long)L.H * L.W;
+  for (int off = 0; off < n; off += 65535) {       // grid.z limit
+    const int cnt = n - off < 65535 ? n - off : 65535;
+    PlaneOut o{};
+    for (int l = 0; l < s->levels; ++l)
+      o.p[l] = reinterpret_cast<float4*>(planes_levels[l]) + (long long)off * (L.H >> l) * (L.W >> l);
+    dim3 grid((L.W + NT_X - 1) / NT_X, (L.H + NT_Y - 1) / NT_Y, cnt);
+    k_normals<<<grid, dim3(NT_X, NT_Y), 0, st>>>(L, s->levels, cnt, range + off * N, rel_jump, o,
+                                                 mask0 ? mask0 + off * N : nullptr);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace rimg

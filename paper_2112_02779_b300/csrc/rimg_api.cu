@@ -1,0 +1,646 @@
+// Host side of librimg: argument checking, sensor tables (step A1), workspace
+// layouts, the multi-scale driver (step A9), the host-buffer variant and
+// launch timing.  Every entry point is declared in include/rimg.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "rimg_internal.h"
+
+namespace rimg {
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int cuda_fail(cudaError_t e, const char* where) {
+  char buf[256];
+  std::snprintf(buf, sizeof(buf), "%s: %s", where, cudaGetErrorString(e));
+  g_last_error = buf;
+  return RIMG_ERR_CUDA;
+}
+
+#define RIMG_CUDA(call)                                  \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
+  } while (0)
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+inline bool aligned(const void* p) { return (reinterpret_cast<uintptr_t>(p) % kAlign) == 0; }
+
+// Byte layout of one level's tables (see rimg_level).
+struct LevelLayout {
+  size_t rows, cols, thu, rank, bnd, bins, end;
+  int n_bins;
+};
+
+LevelLayout level_layout(int Hl, int Wl, size_t start) {
+  LevelLayout L{};
+  L.n_bins = 8 * Hl;
+  size_t o = align_up(start);
+  L.rows = o; o = align_up(o + sizeof(float4) * Hl);
+  L.cols = o; o = align_up(o + sizeof(float2) * Wl);
+  L.thu = o; o = align_up(o + sizeof(float) * Hl);
+  L.rank = o; o = align_up(o + sizeof(int) * Hl);
+  L.bnd = o; o = align_up(o + sizeof(float) * std::max(1, Hl - 1));
+  L.bins = o; o = align_up(o + sizeof(int) * L.n_bins);
+  L.end = o;
+  return L;
+}
+
+int check_dims(int H, int W, int levels) {
+  if (H <= 0 || W <= 0 || levels < 1 || levels > RIMG_MAX_LEVELS) return RIMG_ERR_INVALID_ARG;
+  if ((H >> (levels - 1)) < 2) return RIMG_ERR_SIZE;
+  if ((H % (1 << (levels - 1))) != 0) return RIMG_ERR_SIZE;
+  if ((W % (4 << (levels - 1))) != 0) return RIMG_ERR_SIZE;
+  return RIMG_OK;
+}
+
+int check_sensor(const rimg_sensor* s) {
+  if (!s || !s->d_tables) return RIMG_ERR_INVALID_ARG;
+  int rc = check_dims(s->H, s->W, s->levels);
+  if (rc) return rc;
+  for (int l = 0; l < s->levels; ++l)
+    if (s->level[l].H != (s->H >> l) || s->level[l].W != (s->W >> l)) return RIMG_ERR_INVALID_ARG;
+  return RIMG_OK;
+}
+
+int check_params(const rimg_params* p) {
+  if (!p) return RIMG_ERR_INVALID_ARG;
+  if (!std::isfinite(p->huber_delta) || !std::isfinite(p->max_corr_dist)) return RIMG_ERR_INVALID_ARG;
+  if (!(p->normal_rel_jump >= 0.f && p->normal_rel_jump < 0.5f)) return RIMG_ERR_INVALID_ARG;
+  if (p->proj_iters < 1 || p->proj_iters > 16) return RIMG_ERR_INVALID_ARG;
+  return RIMG_OK;
+}
+
+// ---- launch timing ----
+struct Prof {
+  std::mutex mu;
+  bool on = false;
+  int cap = 0, n = 0;
+  bool open = false;
+  std::vector<cudaEvent_t> ev0, ev1;
+  std::vector<int> kid, lvl, np;
+} g_prof;
+
+}  // namespace
+
+void prof_before(cudaStream_t st, int kernel, int level, int n) {
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  if (!g_prof.on || g_prof.n >= g_prof.cap) return;
+  const int i = g_prof.n;
+  cudaEventRecord(g_prof.ev0[i], st);
+  g_prof.kid[i] = kernel;
+  g_prof.lvl[i] = level;
+  g_prof.np[i] = n;
+  g_prof.open = true;
+}
+
+void prof_after(cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  if (!g_prof.on || !g_prof.open) return;
+  cudaEventRecord(g_prof.ev1[g_prof.n], st);
+  g_prof.open = false;
+  ++g_prof.n;
+}
+
+DevLevel dev_level(const rimg_sensor* s, int l) {
+  const rimg_level& L = s->level[l];
+  const char* base = static_cast<const char*>(s->d_tables);
+  DevLevel d;
+  d.rows = reinterpret_cast<const float4*>(base + L.off_rows);
+  d.cols = reinterpret_cast<const float2*>(base + L.off_cols);
+  d.thu = reinterpret_cast<const float*>(base + L.off_thu);
+  d.rank2row = reinterpret_cast<const int*>(base + L.off_rank);
+  d.bnd = reinterpret_cast<const float*>(base + L.off_bnd);
+  d.bins = reinterpret_cast<const int*>(base + L.off_bins);
+  d.H = L.H;
+  d.W = L.W;
+  d.n_bins = L.n_bins;
+  d.tie_up = L.tie_up;
+  d.s_lo = L.s_lo;
+  d.s_hi = L.s_hi;
+  d.bin_scale = L.bin_scale;
+  d.w_over_2pi = L.w_over_2pi;
+  d.r0 = s->r0;
+  d.inv_w2 = 2.0f / (float)L.W;
+  return d;
+}
+
+// ---- workspace layouts ----
+namespace {
+
+struct IcpWs {
+  size_t counters, partials, end;
+};
+
+IcpWs icp_ws(int H, int n_pairs, size_t start) {
+  IcpWs w{};
+  size_t o = align_up(start);
+  w.counters = o; o = align_up(o + sizeof(unsigned) * (size_t)std::max(n_pairs, 1));
+  w.partials = o; o = align_up(o + sizeof(float) * kRedStride * (size_t)H * std::max(n_pairs, 1));
+  w.end = o;
+  return w;
+}
+
+struct RegWs {
+  size_t src_lvl[RIMG_MAX_LEVELS];   // level >= 1 source ranges
+  size_t planes[RIMG_MAX_LEVELS];    // target planes, all levels
+  IcpWs icp;
+  size_t end;
+};
+
+RegWs reg_ws(int H, int W, int n_pairs, int levels, size_t start) {
+  RegWs r{};
+  size_t o = align_up(start);
+  const size_t n = (size_t)std::max(n_pairs, 0);
+  for (int l = 0; l < levels; ++l) {
+    const size_t Nl = (size_t)(H >> l) * (W >> l);
+    if (l >= 1) { r.src_lvl[l] = o; o = align_up(o + sizeof(float) * Nl * n); }
+    r.planes[l] = o; o = align_up(o + sizeof(float4) * Nl * n);
+  }
+  r.icp = icp_ws(H, n_pairs, o);
+  r.end = r.icp.end;
+  return r;
+}
+
+int icp_launch(const rimg_sensor* src, const rimg_sensor* dst, int level, int n_pairs,
+               const float* src_range_l, const float* dst_planes_l, const float* dst_range_l,
+               double* pose, const rimg_params* p, int update, double* out29, int32_t* assoc,
+               int* status, char* ws, const IcpWs& w, cudaStream_t st) {
+  IcpLaunch a{};
+  a.src = dev_level(src, level);
+  a.dst = dev_level(dst, level);
+  a.n_pairs = n_pairs;
+  a.src_range = src_range_l;
+  a.dst_planes = reinterpret_cast<const float4*>(dst_planes_l);
+  a.dst_range = dst_range_l;
+  a.pose = pose;
+  a.out29 = out29;
+  a.assoc = assoc;
+  a.status = status;
+  a.partials = reinterpret_cast<float*>(ws + w.partials);
+  a.counters = reinterpret_cast<unsigned*>(ws + w.counters);
+  a.huber_delta = p->huber_delta;
+  a.max_corr_dist = p->max_corr_dist;
+  a.proj_iters = p->proj_iters;
+  a.kahan = p->kahan;
+  a.update = update;
+  icp_grid(a.src.H, a.src.W, n_pairs, &a.bpp, &a.rows_per_block);
+  prof_before(st, K_ICP, level, n_pairs);
+  cudaError_t e = launch_icp(a, st);
+  prof_after(st);
+  if (e != cudaSuccess) return cuda_fail(e, "icp step kernel");
+  return RIMG_OK;
+}
+
+int register_device(const rimg_sensor* src, const rimg_sensor* dst, int n_pairs, const float* src_range,
+                    const float* dst_range, const double* T_init, double* T_out, int levels,
+                    const int* iters, const rimg_params* p, int* status, char* ws,
+                    const RegWs& R, cudaStream_t st) {
+  const int H = src->H, W = src->W;
+  if (status) RIMG_CUDA(cudaMemsetAsync(status, 0, sizeof(int) * n_pairs, st));
+  if (T_out != T_init)
+    RIMG_CUDA(cudaMemcpyAsync(T_out, T_init, sizeof(double) * 16 * n_pairs, cudaMemcpyDeviceToDevice, st));
+  RIMG_CUDA(cudaMemsetAsync(ws + R.icp.counters, 0, sizeof(unsigned) * n_pairs, st));
+  // Target planes of every level (normals at the finest level, strided pyramid).
+  float* planes[RIMG_MAX_LEVELS] = {};
+  float* srcl[RIMG_MAX_LEVELS] = {};
+  for (int l = 0; l < levels; ++l) {
+    planes[l] = reinterpret_cast<float*>(ws + R.planes[l]);
+    if (l >= 1) srcl[l] = reinterpret_cast<float*>(ws + R.src_lvl[l]);
+  }
+  // rimg_normals writes every level of dst's table set; register may use fewer
+  // levels than the sensor has, so build a view limited to `levels`.
+  rimg_sensor dview = *dst;
+  dview.levels = levels;
+  prof_before(st, K_NORMALS, 0, n_pairs);
+  cudaError_t e = launch_normals(&dview, n_pairs, dst_range, p->normal_rel_jump, planes, nullptr, st);
+  prof_after(st);
+  if (e != cudaSuccess) return cuda_fail(e, "normals kernel");
+  if (levels > 1) {
+    prof_before(st, K_SRC_PYRAMID, 1, n_pairs);
+    e = launch_pyramid(n_pairs, H, W, levels, 1, src_range, srcl, st);
+    prof_after(st);
+    if (e != cudaSuccess) return cuda_fail(e, "pyramid kernel");
+  }
+  for (int k = 0; k < levels; ++k) {
+    const int l = levels - 1 - k;
+    const float* s_l = (l == 0) ? src_range : srcl[l];
+    for (int it = 0; it < iters[k]; ++it) {
+      int rc = icp_launch(src, dst, l, n_pairs, s_l, planes[l], nullptr, T_out, p, 1, nullptr, nullptr,
+                          status, ws, R.icp, st);
+      if (rc) return rc;
+    }
+  }
+  return RIMG_OK;
+}
+
+int check_register_args(const rimg_sensor* src, const rimg_sensor* dst, int n_pairs, int levels,
+                        const int* iters, const rimg_params* p) {
+  int rc = check_sensor(src);
+  if (rc) return rc;
+  rc = check_sensor(dst);
+  if (rc) return rc;
+  if ((rc = check_params(p))) return rc;
+  if (n_pairs < 0 || !iters) return RIMG_ERR_INVALID_ARG;
+  if (src->H != dst->H || src->W != dst->W) return RIMG_ERR_MISMATCH;
+  if (levels < 1 || levels > src->levels || levels > dst->levels) return RIMG_ERR_INVALID_ARG;
+  for (int k = 0; k < levels; ++k)
+    if (iters[k] < 0 || iters[k] > 100000) return RIMG_ERR_INVALID_ARG;
+  return RIMG_OK;
+}
+
+// Host-buffer variant: a copy stream and events, created once per process.
+struct HostPipe {
+  std::mutex mu;
+  bool ready = false;
+  int device = -1;
+  cudaStream_t copy = nullptr;
+  cudaEvent_t loaded[2] = {nullptr, nullptr};
+  cudaEvent_t freed[2] = {nullptr, nullptr};
+} g_pipe;
+
+}  // namespace
+}  // namespace rimg
+
+using namespace rimg;
+
+extern "C" {
+
+int rimg_default_params(rimg_params* p) {
+  if (!p) return RIMG_ERR_INVALID_ARG;
+  p->huber_delta = 0.5f;
+  p->max_corr_dist = 0.f;
+  p->normal_rel_jump = 0.1f;
+  p->proj_iters = 3;
+  p->kahan = 1;
+  return RIMG_OK;
+}
+
+const char* rimg_status_string(int code) {
+  switch (code) {
+    case RIMG_OK: return "ok";
+    case RIMG_ERR_INVALID_ARG: return "invalid argument";
+    case RIMG_ERR_LUT: return "elevation table not strictly monotone or out of range";
+    case RIMG_ERR_SIZE: return "image size incompatible with the pyramid";
+    case RIMG_ERR_WORKSPACE: return "workspace too small or misaligned";
+    case RIMG_ERR_CUDA: return "CUDA error";
+    case RIMG_ERR_MISMATCH: return "source and target sensors disagree";
+    default: return "unknown status";
+  }
+}
+
+const char* rimg_last_error(void) { return g_last_error.c_str(); }
+
+int rimg_sensor_table_bytes(int H, int W, int levels, size_t* bytes) {
+  if (!bytes) return RIMG_ERR_INVALID_ARG;
+  int rc = check_dims(H, W, levels);
+  if (rc) return rc;
+  size_t o = 0;
+  for (int l = 0; l < levels; ++l) o = level_layout(H >> l, W >> l, o).end;
+  *bytes = o;
+  return RIMG_OK;
+}
+
+int rimg_sensor_build(int H, int W, int levels, const double* phi_lut, const double* theta_lut,
+                      double r0, void* d_tables, size_t table_bytes, rimg_sensor* out) {
+  if (!phi_lut || !theta_lut || !d_tables || !out) return RIMG_ERR_INVALID_ARG;
+  int rc = check_dims(H, W, levels);
+  if (rc) return rc;
+  if (!std::isfinite(r0) || r0 < 0.0) return RIMG_ERR_INVALID_ARG;
+  if (!aligned(d_tables)) return RIMG_ERR_WORKSPACE;
+  const double kHalfPi = 1.5707963267948966, kPi = 3.141592653589793;
+  for (int v = 0; v < H; ++v) {
+    if (!std::isfinite(phi_lut[v]) || std::fabs(phi_lut[v]) >= kHalfPi) return RIMG_ERR_LUT;
+    if (!std::isfinite(theta_lut[v]) || std::fabs(theta_lut[v]) >= kPi) return RIMG_ERR_LUT;
+  }
+  const bool desc = H > 1 && phi_lut[1] < phi_lut[0];
+  for (int v = 1; v < H; ++v) {
+    if (desc ? !(phi_lut[v] < phi_lut[v - 1]) : !(phi_lut[v] > phi_lut[v - 1])) return RIMG_ERR_LUT;
+  }
+  size_t need = 0;
+  rimg_sensor_table_bytes(H, W, levels, &need);
+  if (table_bytes < need) return RIMG_ERR_WORKSPACE;
+
+  rimg_sensor s{};
+  s.H = H;
+  s.W = W;
+  s.levels = levels;
+  s.r0 = (float)r0;
+  s.d_tables = d_tables;
+  s.table_bytes = need;
+  std::vector<unsigned char> buf(need, 0);
+  size_t o = 0;
+  for (int l = 0; l < levels; ++l) {
+    const int Hl = H >> l, Wl = W >> l;
+    const LevelLayout L = level_layout(Hl, Wl, o);
+    o = L.end;
+    std::vector<double> ph(Hl), th(Hl);
+    for (int v = 0; v < Hl; ++v) {
+      ph[v] = phi_lut[v << l];
+      th[v] = theta_lut[v << l];
+    }
+    float4* rows = reinterpret_cast<float4*>(buf.data() + L.rows);
+    float2* cols = reinterpret_cast<float2*>(buf.data() + L.cols);
+    float* thu = reinterpret_cast<float*>(buf.data() + L.thu);
+    int* rank = reinterpret_cast<int*>(buf.data() + L.rank);
+    float* bnd = reinterpret_cast<float*>(buf.data() + L.bnd);
+    int* bins = reinterpret_cast<int*>(buf.data() + L.bins);
+    for (int v = 0; v < Hl; ++v) {
+      rows[v] = make_float4((float)std::cos(ph[v]), (float)std::sin(ph[v]), (float)std::cos(th[v]),
+                            (float)std::sin(th[v]));
+      thu[v] = (float)(th[v] * Wl / (2.0 * kPi));
+    }
+    for (int u = 0; u < Wl; ++u) {
+      const double a = 2.0 * kPi * ((double)u / (double)Wl);
+      cols[u] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
+    // rank j = j-th smallest elevation
+    std::vector<int> order(Hl);
+    std::iota(order.begin(), order.end(), 0);
+    std::sort(order.begin(), order.end(), [&](int a, int b) { return ph[a] < ph[b]; });
+    for (int j = 0; j < Hl; ++j) rank[j] = order[j];
+    std::vector<double> asc(Hl);
+    for (int j = 0; j < Hl; ++j) asc[j] = ph[order[j]];
+    for (int j = 0; j + 1 < Hl; ++j) bnd[j] = (float)std::sin(0.5 * (asc[j] + asc[j + 1]));
+    double lo = asc[0] - 0.5 * (asc[1] - asc[0]);
+    double hi = asc[Hl - 1] + 0.5 * (asc[Hl - 1] - asc[Hl - 2]);
+    lo = std::max(lo, -kHalfPi);
+    hi = std::min(hi, kHalfPi);
+    rimg_level& lv = s.level[l];
+    lv.H = Hl;
+    lv.W = Wl;
+    lv.n_bins = L.n_bins;
+    lv.tie_up = desc ? 1 : 0;
+    lv.s_lo = (float)std::sin(lo);
+    lv.s_hi = (float)std::sin(hi);
+    lv.bin_scale = (float)((double)L.n_bins / ((double)lv.s_hi - (double)lv.s_lo));
+    lv.w_over_2pi = (float)((double)Wl / (2.0 * kPi));
+    for (int b = 0; b < L.n_bins; ++b) {
+      const double edge = (double)lv.s_lo + (double)b / (double)lv.bin_scale;
+      int j = 0;
+      while (j < Hl - 1 && (double)bnd[j] < edge) ++j;
+      bins[b] = j;
+    }
+    lv.off_rows = L.rows;
+    lv.off_cols = L.cols;
+    lv.off_thu = L.thu;
+    lv.off_rank = L.rank;
+    lv.off_bnd = L.bnd;
+    lv.off_bins = L.bins;
+  }
+  RIMG_CUDA(cudaMemcpy(d_tables, buf.data(), need, cudaMemcpyHostToDevice));
+  *out = s;
+  return RIMG_OK;
+}
+
+int rimg_unproject(const rimg_sensor* s, int level, int n_images, const float* range, float* xyz,
+                   uint8_t* mask, void* stream) {
+  int rc = check_sensor(s);
+  if (rc) return rc;
+  if (level < 0 || level >= s->levels || n_images < 0) return RIMG_ERR_INVALID_ARG;
+  if (n_images == 0) return RIMG_OK;
+  if (!range || !xyz) return RIMG_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  prof_before(st, K_UNPROJECT, level, n_images);
+  cudaError_t e = launch_unproject(dev_level(s, level), n_images, range, xyz, mask, st);
+  prof_after(st);
+  if (e != cudaSuccess) return cuda_fail(e, "unproject kernel");
+  return RIMG_OK;
+}
+
+int rimg_pyramid(int n_images, int H, int W, int levels, int channels, const float* in,
+                 float* const* out_levels, void* stream) {
+  if (n_images < 0 || H <= 0 || W <= 0 || levels < 1 || levels > RIMG_MAX_LEVELS) return RIMG_ERR_INVALID_ARG;
+  if (channels != 1 && channels != 4) return RIMG_ERR_INVALID_ARG;
+  if ((H % (1 << (levels - 1))) || (W % (1 << (levels - 1)))) return RIMG_ERR_SIZE;
+  if (n_images == 0 || levels == 1) return RIMG_OK;
+  if (!in || !out_levels) return RIMG_ERR_INVALID_ARG;
+  for (int l = 1; l < levels; ++l)
+    if (!out_levels[l]) return RIMG_ERR_INVALID_ARG;
+  if (channels == 4) {
+    if (reinterpret_cast<uintptr_t>(in) % 16) return RIMG_ERR_INVALID_ARG;
+    for (int l = 1; l < levels; ++l)
+      if (reinterpret_cast<uintptr_t>(out_levels[l]) % 16) return RIMG_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  prof_before(st, K_PYRAMID, 1, n_images);
+  cudaError_t e = launch_pyramid(n_images, H, W, levels, channels, in, out_levels, st);
+  prof_after(st);
+  if (e != cudaSuccess) return cuda_fail(e, "pyramid kernel");
+  return RIMG_OK;
+}
+
+int rimg_normals(const rimg_sensor* s, int n_images, const float* range, const rimg_params* p,
+                 float* const* planes_levels, uint8_t* mask0, void* stream) {
+  int rc = check_sensor(s);
+  if (rc) return rc;
+  if ((rc = check_params(p))) return rc;
+  if (n_images < 0) return RIMG_ERR_INVALID_ARG;
+  if (n_images == 0) return RIMG_OK;
+  if (!range || !planes_levels) return RIMG_ERR_INVALID_ARG;
+  for (int l = 0; l < s->levels; ++l)
+    if (!planes_levels[l]) return RIMG_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  prof_before(st, K_NORMALS, 0, n_images);
+  cudaError_t e = launch_normals(s, n_images, range, p->normal_rel_jump, planes_levels, mask0, st);
+  prof_after(st);
+  if (e != cudaSuccess) return cuda_fail(e, "normals kernel");
+  return RIMG_OK;
+}
+
+int rimg_icp_workspace_bytes(const rimg_sensor* src, int n_pairs, size_t* bytes) {
+  if (!bytes) return RIMG_ERR_INVALID_ARG;
+  int rc = check_sensor(src);
+  if (rc) return rc;
+  if (n_pairs < 0) return RIMG_ERR_INVALID_ARG;
+  *bytes = icp_ws(src->H, n_pairs, 0).end;
+  return RIMG_OK;
+}
+
+int rimg_icp_step(const rimg_sensor* src, const rimg_sensor* dst, int level, int n_pairs,
+                  const float* src_range_l, const float* dst_planes_l, const float* dst_range_l,
+                  double* pose, const rimg_params* p, int update, double* out29, int32_t* assoc,
+                  int* status, void* workspace, size_t workspace_bytes, void* stream) {
+  int rc = check_sensor(src);
+  if (rc) return rc;
+  if ((rc = check_sensor(dst))) return rc;
+  if ((rc = check_params(p))) return rc;
+  if (src->levels != dst->levels) return RIMG_ERR_MISMATCH;
+  if (level < 0 || level >= src->levels || n_pairs < 0) return RIMG_ERR_INVALID_ARG;
+  if (n_pairs == 0) return RIMG_OK;
+  if (!src_range_l || !dst_planes_l || !pose || !workspace) return RIMG_ERR_INVALID_ARG;
+  if (p->max_corr_dist > 0.f && !dst_range_l) return RIMG_ERR_INVALID_ARG;
+  const IcpWs w = icp_ws(src->H, n_pairs, 0);
+  if (!aligned(workspace) || workspace_bytes < w.end) return RIMG_ERR_WORKSPACE;
+  if ((reinterpret_cast<uintptr_t>(src_range_l) % 16) || (reinterpret_cast<uintptr_t>(dst_planes_l) % 16) ||
+      (assoc && (reinterpret_cast<uintptr_t>(assoc) % 16)))
+    return RIMG_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  char* ws = static_cast<char*>(workspace);
+  RIMG_CUDA(cudaMemsetAsync(ws + w.counters, 0, sizeof(unsigned) * n_pairs, st));
+  return icp_launch(src, dst, level, n_pairs, src_range_l, dst_planes_l, dst_range_l, pose, p, update,
+                    out29, assoc, status, ws, w, st);
+}
+
+int rimg_register_workspace_bytes(const rimg_sensor* src, const rimg_sensor* dst, int n_pairs, int levels,
+                                  size_t* bytes) {
+  if (!bytes) return RIMG_ERR_INVALID_ARG;
+  int rc = check_sensor(src);
+  if (rc) return rc;
+  if ((rc = check_sensor(dst))) return rc;
+  if (src->H != dst->H || src->W != dst->W) return RIMG_ERR_MISMATCH;
+  if (n_pairs < 0 || levels < 1 || levels > src->levels || levels > dst->levels) return RIMG_ERR_INVALID_ARG;
+  *bytes = reg_ws(src->H, src->W, n_pairs, levels, 0).end;
+  return RIMG_OK;
+}
+
+int rimg_register(const rimg_sensor* src, const rimg_sensor* dst, int n_pairs, const float* src_range,
+                  const float* dst_range, const double* T_init, double* T_out, int levels, const int* iters,
+                  const rimg_params* p, int* status, void* workspace, size_t workspace_bytes, void* stream) {
+  int rc = check_register_args(src, dst, n_pairs, levels, iters, p);
+  if (rc) return rc;
+  if (n_pairs == 0) return RIMG_OK;
+  if (!src_range || !dst_range || !T_init || !T_out || !workspace) return RIMG_ERR_INVALID_ARG;
+  if ((reinterpret_cast<uintptr_t>(src_range) % 16) || (reinterpret_cast<uintptr_t>(dst_range) % 16))
+    return RIMG_ERR_INVALID_ARG;
+  const RegWs R = reg_ws(src->H, src->W, n_pairs, levels, 0);
+  if (!aligned(workspace) || workspace_bytes < R.end) return RIMG_ERR_WORKSPACE;
+  return register_device(src, dst, n_pairs, src_range, dst_range, T_init, T_out, levels, iters, p, status,
+                         static_cast<char*>(workspace), R, static_cast<cudaStream_t>(stream));
+}
+
+int rimg_register_host_workspace_bytes(const rimg_sensor* src, const rimg_sensor* dst, int n_pairs, int levels,
+                                       int chunk_pairs, size_t* bytes) {
+  if (!bytes) return RIMG_ERR_INVALID_ARG;
+  int rc = check_sensor(src);
+  if (rc) return rc;
+  if ((rc = check_sensor(dst))) return rc;
+  if (src->H != dst->H || src->W != dst->W) return RIMG_ERR_MISMATCH;
+  if (n_pairs < 0 || levels < 1 || levels > src->levels || levels > dst->levels) return RIMG_ERR_INVALID_ARG;
+  const int chunk = (chunk_pairs <= 0 || chunk_pairs > n_pairs) ? std::max(n_pairs, 1) : chunk_pairs;
+  const size_t N = (size_t)src->H * src->W;
+  size_t o = 0;
+  for (int b = 0; b < 2; ++b) o = align_up(o + sizeof(float) * N * chunk * 2);   // src + dst per buffer
+  o = align_up(o + sizeof(double) * 16 * std::max(n_pairs, 1));
+  o = align_up(o + sizeof(int) * std::max(n_pairs, 1));
+  *bytes = reg_ws(src->H, src->W, chunk, levels, o).end;
+  return RIMG_OK;
+}
+
+int rimg_register_host(const rimg_sensor* src, const rimg_sensor* dst, int n_pairs, const float* src_range_host,
+                       const float* dst_range_host, const double* T_init_host, double* T_out_host, int levels,
+                       const int* iters, const rimg_params* p, int* status_host, int chunk_pairs, void* workspace,
+                       size_t workspace_bytes, void* stream) {
+  int rc = check_register_args(src, dst, n_pairs, levels, iters, p);
+  if (rc) return rc;
+  if (n_pairs == 0) return RIMG_OK;
+  if (!src_range_host || !dst_range_host || !T_init_host || !T_out_host || !workspace) return RIMG_ERR_INVALID_ARG;
+  size_t need = 0;
+  rimg_register_host_workspace_bytes(src, dst, n_pairs, levels, chunk_pairs, &need);
+  if (!aligned(workspace) || workspace_bytes < need) return RIMG_ERR_WORKSPACE;
+  const int chunk = (chunk_pairs <= 0 || chunk_pairs > n_pairs) ? n_pairs : chunk_pairs;
+  const size_t N = (size_t)src->H * src->W;
+  char* ws = static_cast<char*>(workspace);
+  size_t o = 0;
+  float* buf[2];
+  for (int b = 0; b < 2; ++b) {
+    buf[b] = reinterpret_cast<float*>(ws + o);
+    o = align_up(o + sizeof(float) * N * chunk * 2);
+  }
+  double* dT = reinterpret_cast<double*>(ws + o);
+  o = align_up(o + sizeof(double) * 16 * n_pairs);
+  int* dS = reinterpret_cast<int*>(ws + o);
+  o = align_up(o + sizeof(int) * n_pairs);
+  const RegWs R = reg_ws(src->H, src->W, chunk, levels, o);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+
+  std::lock_guard<std::mutex> lk(g_pipe.mu);
+  int dev = 0;
+  RIMG_CUDA(cudaGetDevice(&dev));
+  if (!g_pipe.ready || g_pipe.device != dev) {
+    RIMG_CUDA(cudaStreamCreateWithFlags(&g_pipe.copy, cudaStreamNonBlocking));
+    for (int b = 0; b < 2; ++b) {
+      RIMG_CUDA(cudaEventCreateWithFlags(&g_pipe.loaded[b], cudaEventDisableTiming));
+      RIMG_CUDA(cudaEventCreateWithFlags(&g_pipe.freed[b], cudaEventDisableTiming));
+    }
+    g_pipe.ready = true;
+    g_pipe.device = dev;
+  }
+  // the copy stream must not run ahead of work already queued on `stream`
+  RIMG_CUDA(cudaEventRecord(g_pipe.freed[0], st));
+  RIMG_CUDA(cudaEventRecord(g_pipe.freed[1], st));
+  RIMG_CUDA(cudaMemcpyAsync(dT, T_init_host, sizeof(double) * 16 * n_pairs, cudaMemcpyHostToDevice, st));
+  int k = 0;
+  for (int off = 0; off < n_pairs; off += chunk, ++k) {
+    const int b = k & 1;
+    const int cnt = std::min(chunk, n_pairs - off);
+    float* d_src = buf[b];
+    float* d_dst = buf[b] + N * chunk;
+    RIMG_CUDA(cudaStreamWaitEvent(g_pipe.copy, g_pipe.freed[b], 0));
+    RIMG_CUDA(cudaMemcpyAsync(d_src, src_range_host + N * off, sizeof(float) * N * cnt, cudaMemcpyHostToDevice,
+                              g_pipe.copy));
+    RIMG_CUDA(cudaMemcpyAsync(d_dst, dst_range_host + N * off, sizeof(float) * N * cnt, cudaMemcpyHostToDevice,
+                              g_pipe.copy));
+    RIMG_CUDA(cudaEventRecord(g_pipe.loaded[b], g_pipe.copy));
+    RIMG_CUDA(cudaStreamWaitEvent(st, g_pipe.loaded[b], 0));
+    rc = register_device(src, dst, cnt, d_src, d_dst, dT + 16 * off, dT + 16 * off, levels, iters, p, dS + off,
+                         ws, R, st);
+    if (rc) return rc;
+    RIMG_CUDA(cudaEventRecord(g_pipe.freed[b], st));
+    RIMG_CUDA(cudaMemcpyAsync(T_out_host + 16 * off, dT + 16 * off, sizeof(double) * 16 * cnt,
+                              cudaMemcpyDeviceToHost, st));
+    if (status_host)
+      RIMG_CUDA(cudaMemcpyAsync(status_host + off, dS + off, sizeof(int) * cnt, cudaMemcpyDeviceToHost, st));
+  }
+  RIMG_CUDA(cudaStreamSynchronize(st));
+  return RIMG_OK;
+}
+
+int rimg_profile_begin(int max_launches) {
+  if (max_launches < 0) return RIMG_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  const int have = (int)g_prof.ev0.size();
+  for (int i = have; i < max_launches; ++i) {
+    cudaEvent_t a, b;
+    RIMG_CUDA(cudaEventCreate(&a));
+    RIMG_CUDA(cudaEventCreate(&b));
+    g_prof.ev0.push_back(a);
+    g_prof.ev1.push_back(b);
+  }
+  g_prof.kid.assign(std::max(have, max_launches), 0);
+  g_prof.lvl.assign(std::max(have, max_launches), 0);
+  g_prof.np.assign(std::max(have, max_launches), 0);
+  g_prof.cap = max_launches;
+  g_prof.n = 0;
+  g_prof.open = false;
+  g_prof.on = true;
+  return RIMG_OK;
+}
+
+int rimg_profile_end(int cap, int* kernel_id, int* level, int* n_pairs, float* ms) {
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  g_prof.on = false;
+  const int n = std::min(cap, g_prof.n);
+  for (int i = 0; i < n; ++i) {
+    RIMG_CUDA(cudaEventSynchronize(g_prof.ev1[i]));
+    float t = 0.f;
+    RIMG_CUDA(cudaEventElapsedTime(&t, g_prof.ev0[i], g_prof.ev1[i]));
+    if (kernel_id) kernel_id[i] = g_prof.kid[i];
+    if (level) level[i] = g_prof.lvl[i];
+    if (n_pairs) n_pairs[i] = g_prof.np[i];
+    if (ms) ms[i] = t;
+  }
+  g_prof.n = 0;
+  return n;
+}
+
+}  // extern "C"

@@ -1,0 +1,65 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include "../../include/rimg.h"
+
+namespace rimg {
+
+// Device view of one pyramid level of a sensor's tables (built on the host
+// from rimg_sensor and passed to kernels by value).
+struct DevLevel {
+  const float4* rows;     // [H] cos phi, sin phi, cos theta_lut, sin theta_lut
+  const float2* cols;     // [W] cos, sin of 2 pi u / W
+  const float* thu;       // [H] theta_lut * W / (2 pi)
+  const int* rank2row;    // [H]
+  const float* bnd;       // [H-1]
+  const int* bins;        // [n_bins]
+  int H, W, n_bins, tie_up;
+  float s_lo, s_hi, bin_scale, w_over_2pi, r0, inv_w2;   // inv_w2 = 2 / W
+};
+
+DevLevel dev_level(const rimg_sensor* s, int level);
+
+enum KernelId { K_UNPROJECT = 0, K_PYRAMID = 1, K_NORMALS = 2, K_ICP = 3, K_SRC_PYRAMID = 4 };
+
+// Launch-timing hooks (no-ops unless rimg_profile_begin was called).
+void prof_before(cudaStream_t st, int kernel, int level, int n);
+void prof_after(cudaStream_t st);
+
+// Launchers (return cudaGetLastError()).
+cudaError_t launch_unproject(const DevLevel& L, int n, const float* range, float* xyz,
+                             uint8_t* mask, cudaStream_t st);
+cudaError_t launch_pyramid(int n, int H, int W, int levels, int channels, const float* in,
+                           float* const* out_levels, cudaStream_t st);
+cudaError_t launch_normals(const rimg_sensor* s, int n, const float* range, float rel_jump,
+                           float* const* planes_levels, uint8_t* mask0, cudaStream_t st);
+
+struct IcpLaunch {
+  DevLevel src, dst;
+  int n_pairs;
+  const float* src_range;
+  const float4* dst_planes;
+  const float* dst_range;
+  double* pose;
+  double* out29;
+  int32_t* assoc;
+  int* status;
+  float* partials;          // [n_pairs][bpp][32]
+  unsigned int* counters;   // [n_pairs]
+  float huber_delta, max_corr_dist;
+  int proj_iters, kahan, update;
+  int bpp, rows_per_block;
+};
+
+// Blocks per pair and rows per block for a level (depends on the batch and
+// the device's resident-block capacity).
+void icp_grid(int H, int W, int n_pairs, int* bpp, int* rows_per_block);
+cudaError_t launch_icp(const IcpLaunch& a, cudaStream_t st);
+
+constexpr int kIcpThreads = 256;
+constexpr int kRed = 29;          // reduced quantities per pair
+constexpr int kRedStride = 32;    // floats per partial record
+
+}  // namespace rimg

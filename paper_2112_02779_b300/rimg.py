@@ -1,0 +1,244 @@
+"""Python binding of librimg (include/rimg.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and forwards
+device pointers taken from torch tensors; all computation happens in the CUDA
+library.  The library must be built (``python -m paper_2112_02779_b300.build``
+or ``__graft_entry__.build()``); importing this package fails loudly if it is
+missing.  torch is used only for device memory and streams.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from ._abi import (RIMG_MAX_LEVELS, RIMG_FLAG_DEGENERATE, rimg_level, rimg_sensor, rimg_params,
+                   STATUS_NAMES, HEADER_FUNCTIONS)
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "librimg.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"librimg.so not built ({LIB_PATH}); run `python -m paper_2112_02779_b300.build`")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+_c_int, _c_size, _vp = ctypes.c_int, ctypes.c_size_t, ctypes.c_void_p
+_P = ctypes.POINTER
+
+
+def _sig(name, restype, *argtypes):
+    f = getattr(_lib, name)
+    f.restype = restype
+    f.argtypes = list(argtypes)
+    return f
+
+
+_sig("rimg_default_params", _c_int, _P(rimg_params))
+_sig("rimg_status_string", ctypes.c_char_p, _c_int)
+_sig("rimg_last_error", ctypes.c_char_p)
+_sig("rimg_sensor_table_bytes", _c_int, _c_int, _c_int, _c_int, _P(_c_size))
+_sig("rimg_sensor_build", _c_int, _c_int, _c_int, _c_int, _P(ctypes.c_double), _P(ctypes.c_double),
+     ctypes.c_double, _vp, _c_size, _P(rimg_sensor))
+_sig("rimg_unproject", _c_int, _P(rimg_sensor), _c_int, _c_int, _vp, _vp, _vp, _vp)
+_sig("rimg_pyramid", _c_int, _c_int, _c_int, _c_int, _c_int, _c_int, _vp, _P(_vp), _vp)
+_sig("rimg_normals", _c_int, _P(rimg_sensor), _c_int, _vp, _P(rimg_params), _P(_vp), _vp, _vp)
+_sig("rimg_icp_workspace_bytes", _c_int, _P(rimg_sensor), _c_int, _P(_c_size))
+_sig("rimg_icp_step", _c_int, _P(rimg_sensor), _P(rimg_sensor), _c_int, _c_int, _vp, _vp, _vp, _vp,
+     _P(rimg_params), _c_int, _vp, _vp, _vp, _vp, _c_size, _vp)
+_sig("rimg_register_workspace_bytes", _c_int, _P(rimg_sensor), _P(rimg_sensor), _c_int, _c_int, _P(_c_size))
+_sig("rimg_register", _c_int, _P(rimg_sensor), _P(rimg_sensor), _c_int, _vp, _vp, _vp, _vp, _c_int,
+     _P(_c_int), _P(rimg_params), _vp, _vp, _c_size, _vp)
+_sig("rimg_register_host_workspace_bytes", _c_int, _P(rimg_sensor), _P(rimg_sensor), _c_int, _c_int,
+     _c_int, _P(_c_size))
+_sig("rimg_register_host", _c_int, _P(rimg_sensor), _P(rimg_sensor), _c_int, _vp, _vp, _vp, _vp, _c_int,
+     _P(_c_int), _P(rimg_params), _vp, _c_int, _vp, _c_size, _vp)
+_sig("rimg_profile_begin", _c_int, _c_int)
+_sig("rimg_profile_end", _c_int, _c_int, _P(_c_int), _P(_c_int), _P(_c_int), _P(ctypes.c_float))
+
+
+class RimgError(RuntimeError):
+    def __init__(self, fn, code):
+        msg = _lib.rimg_status_string(code).decode()
+        extra = _lib.rimg_last_error().decode() if code == -5 else ""
+        super().__init__(f"{fn} failed: {code} ({msg}){': ' + extra if extra else ''}")
+        self.code = code
+
+
+def _check(fn, code):
+    if code != 0:
+        raise RimgError(fn, code)
+
+
+def lib():
+    """The loaded ctypes library (for tests that call entry points raw)."""
+    return _lib
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _ptr_array(tensors, n):
+    arr = (_vp * n)()
+    for i, t in enumerate(tensors):
+        arr[i] = _ptr(t) if t is not None else None
+    return arr
+
+
+# ---------------------------------------------------------------------------
+
+def rimg_default_params(**overrides):
+    p = rimg_params()
+    _check("rimg_default_params", _lib.rimg_default_params(ctypes.byref(p)))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def rimg_status_string(code):
+    return _lib.rimg_status_string(code).decode()
+
+
+def rimg_sensor_table_bytes(H, W, levels):
+    b = _c_size(0)
+    _check("rimg_sensor_table_bytes", _lib.rimg_sensor_table_bytes(H, W, levels, ctypes.byref(b)))
+    return b.value
+
+
+class Sensor:
+    """A built sensor: the rimg_sensor struct plus the torch tensor holding its
+    device tables (kept alive with the struct)."""
+
+    def __init__(self, struct, tables):
+        self.struct = struct
+        self.tables = tables
+
+    @property
+    def H(self):
+        return self.struct.H
+
+    @property
+    def W(self):
+        return self.struct.W
+
+    @property
+    def levels(self):
+        return self.struct.levels
+
+    def ref(self):
+        return ctypes.byref(self.struct)
+
+
+def rimg_sensor_build(H, W, levels, phi_lut, theta_lut, r0, device="cuda"):
+    import torch
+    nbytes = rimg_sensor_table_bytes(H, W, levels)
+    tables = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device)
+    phi = np.ascontiguousarray(phi_lut, dtype=np.float64)
+    th = np.ascontiguousarray(theta_lut, dtype=np.float64)
+    s = rimg_sensor()
+    _check("rimg_sensor_build", _lib.rimg_sensor_build(
+        H, W, levels, phi.ctypes.data_as(_P(ctypes.c_double)), th.ctypes.data_as(_P(ctypes.c_double)),
+        float(r0), tables.data_ptr(), tables.numel(), ctypes.byref(s)))
+    return Sensor(s, tables)
+
+
+def rimg_unproject(sensor, level, range_l, xyz, mask=None, stream=None):
+    n = range_l.shape[0] if range_l.dim() == 3 else 1
+    _check("rimg_unproject", _lib.rimg_unproject(sensor.ref(), level, n, _ptr(range_l), _ptr(xyz), _ptr(mask),
+                                                 _stream(stream)))
+
+
+def rimg_pyramid(n_images, H, W, levels, channels, inp, out_levels, stream=None):
+    arr = _ptr_array(out_levels, RIMG_MAX_LEVELS)
+    _check("rimg_pyramid", _lib.rimg_pyramid(n_images, H, W, levels, channels, _ptr(inp), arr, _stream(stream)))
+
+
+def rimg_normals(sensor, range_img, params, planes_levels, mask0=None, stream=None):
+    n = range_img.shape[0] if range_img.dim() == 3 else 1
+    arr = _ptr_array(planes_levels, RIMG_MAX_LEVELS)
+    _check("rimg_normals", _lib.rimg_normals(sensor.ref(), n, _ptr(range_img), ctypes.byref(params), arr,
+                                             _ptr(mask0), _stream(stream)))
+
+
+def rimg_icp_workspace_bytes(src, n_pairs):
+    b = _c_size(0)
+    _check("rimg_icp_workspace_bytes", _lib.rimg_icp_workspace_bytes(src.ref(), n_pairs, ctypes.byref(b)))
+    return b.value
+
+
+def rimg_icp_step(src, dst, level, n_pairs, src_range_l, dst_planes_l, dst_range_l, pose, params, update,
+                  out29=None, assoc=None, status=None, workspace=None, stream=None):
+    _check("rimg_icp_step", _lib.rimg_icp_step(
+        src.ref(), dst.ref(), level, n_pairs, _ptr(src_range_l), _ptr(dst_planes_l), _ptr(dst_range_l),
+        _ptr(pose), ctypes.byref(params), int(update), _ptr(out29), _ptr(assoc), _ptr(status),
+        _ptr(workspace), workspace.numel() if workspace is not None else 0, _stream(stream)))
+
+
+def rimg_register_workspace_bytes(src, dst, n_pairs, levels):
+    b = _c_size(0)
+    _check("rimg_register_workspace_bytes",
+           _lib.rimg_register_workspace_bytes(src.ref(), dst.ref(), n_pairs, levels, ctypes.byref(b)))
+    return b.value
+
+
+def _iters(iters):
+    return (_c_int * len(iters))(*[int(i) for i in iters])
+
+
+def rimg_register(src, dst, n_pairs, src_range, dst_range, T_init, T_out, levels, iters, params, status=None,
+                  workspace=None, stream=None):
+    _check("rimg_register", _lib.rimg_register(
+        src.ref(), dst.ref(), n_pairs, _ptr(src_range), _ptr(dst_range), _ptr(T_init), _ptr(T_out), levels,
+        _iters(iters), ctypes.byref(params), _ptr(status), _ptr(workspace),
+        workspace.numel() if workspace is not None else 0, _stream(stream)))
+
+
+def rimg_register_host_workspace_bytes(src, dst, n_pairs, levels, chunk_pairs=0):
+    b = _c_size(0)
+    _check("rimg_register_host_workspace_bytes", _lib.rimg_register_host_workspace_bytes(
+        src.ref(), dst.ref(), n_pairs, levels, chunk_pairs, ctypes.byref(b)))
+    return b.value
+
+
+def rimg_register_host(src, dst, n_pairs, src_range_host, dst_range_host, T_init_host, T_out_host, levels, iters,
+                       params, status_host=None, chunk_pairs=0, workspace=None, stream=None):
+    """Host tensors (ideally pinned) in and out; synchronises the stream."""
+    _check("rimg_register_host", _lib.rimg_register_host(
+        src.ref(), dst.ref(), n_pairs, _ptr(src_range_host), _ptr(dst_range_host), _ptr(T_init_host),
+        _ptr(T_out_host), levels, _iters(iters), ctypes.byref(params), _ptr(status_host), int(chunk_pairs),
+        _ptr(workspace), workspace.numel() if workspace is not None else 0, _stream(stream)))
+
+
+def rimg_profile_begin(max_launches):
+    _check("rimg_profile_begin", _lib.rimg_profile_begin(max_launches))
+
+
+def rimg_profile_end(cap=100000):
+    """Returns a list of (kernel_id, level, n_pairs, ms) records."""
+    kid = (_c_int * cap)()
+    lvl = (_c_int * cap)()
+    npr = (_c_int * cap)()
+    ms = (ctypes.c_float * cap)()
+    n = _lib.rimg_profile_end(cap, kid, lvl, npr, ms)
+    if n < 0:
+        raise RimgError("rimg_profile_end", n)
+    return [(kid[i], lvl[i], npr[i], ms[i]) for i in range(n)]
+
+
+KERNEL_NAMES = {0: "unproject", 1: "pyramid", 2: "normals", 3: "icp_step", 4: "src_pyramid"}
+
+__all__ = [n for n in dir() if n.startswith("rimg_")] + ["Sensor", "RimgError", "KERNEL_NAMES",
+                                                          "RIMG_MAX_LEVELS", "RIMG_FLAG_DEGENERATE", "lib"]

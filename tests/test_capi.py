@@ -1,0 +1,117 @@
+"""The C ABI on the CPU: the library loads, exports every function the header
+declares, its structs match the Python mirrors, and host-side argument checks
+reject bad input before any CUDA call (no GPU needed)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from tests.conftest import ROOT
+
+R = pytest.importorskip("paper_2112_02779_b300.rimg")
+from paper_2112_02779_b300 import _abi  # noqa: E402
+
+HEADER = os.path.join(ROOT, "include", "rimg.h")
+
+
+def _declared():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(rimg_\w+)\s*\(", txt, flags=re.M)))
+
+
+def test_header_declarations_are_exported():
+    names = _declared()
+    assert sorted(names) == sorted(_abi.HEADER_FUNCTIONS)
+    out = subprocess.run(["nm", "-D", "--defined-only", R.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\sT\s(rimg_\w+)", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    for n in names:
+        assert hasattr(R.lib(), n)
+
+
+def test_struct_layout_matches_header(tmp_path):
+    src = tmp_path / "layout.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "rimg.h"
+int main(void) {
+  printf("%zu %zu %zu\n", sizeof(rimg_level), sizeof(rimg_sensor), sizeof(rimg_params));
+  printf("%zu %zu %zu %zu\n", offsetof(rimg_level, off_rows), offsetof(rimg_level, off_bins),
+         offsetof(rimg_sensor, d_tables), offsetof(rimg_sensor, level));
+  printf("%zu %zu\n", offsetof(rimg_params, proj_iters), offsetof(rimg_params, kahan));
+  return 0;
+}
+''')
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    vals = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
+    L, S, P = _abi.rimg_level, _abi.rimg_sensor, _abi.rimg_params
+    assert vals == [ctypes.sizeof(L), ctypes.sizeof(S), ctypes.sizeof(P),
+                    L.off_rows.offset, L.off_bins.offset, S.d_tables.offset, S.level.offset,
+                    P.proj_iters.offset, P.kahan.offset]
+
+
+def test_default_params_and_status_strings():
+    p = R.rimg_default_params()
+    assert p.huber_delta == pytest.approx(0.5) and p.max_corr_dist == 0.0
+    assert p.normal_rel_jump == pytest.approx(0.1) and p.proj_iters == 3 and p.kahan == 1
+    for code in _abi.STATUS_NAMES:
+        assert R.rimg_status_string(code)
+    assert R.rimg_status_string(12345) == "unknown status"
+
+
+def test_table_bytes_size_rules():
+    lib = R.lib()
+    b = ctypes.c_size_t()
+    assert lib.rimg_sensor_table_bytes(64, 1024, 4, ctypes.byref(b)) == 0 and b.value > 0
+    assert lib.rimg_sensor_table_bytes(64, 1000, 4, ctypes.byref(b)) == -3      # W % (4 << 3)
+    assert lib.rimg_sensor_table_bytes(4, 1024, 4, ctypes.byref(b)) == -3       # H >> 3 < 2
+    assert lib.rimg_sensor_table_bytes(64, 1024, 9, ctypes.byref(b)) == -1      # too many levels
+    assert lib.rimg_sensor_table_bytes(64, 1024, 4, None) == -1
+
+
+def _build_raw(phi, theta, r0=0.0, H=None, W=64, levels=1, dptr=4096, nbytes=1 << 20):
+    H = len(phi) if H is None else H
+    phi = np.ascontiguousarray(phi, np.float64)
+    theta = np.ascontiguousarray(theta, np.float64)
+    s = _abi.rimg_sensor()
+    return R.lib().rimg_sensor_build(H, W, levels, phi.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                     theta.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), r0, dptr, nbytes,
+                                     ctypes.byref(s))
+
+
+def test_sensor_build_rejects_bad_tables_before_touching_the_device():
+    # the device pointer is fake: these calls must fail in host-side checks
+    H = 8
+    good = np.deg2rad(np.linspace(10, -20, H))
+    bad = good.copy()
+    bad[3] = bad[2]                                   # not strictly monotone
+    assert _build_raw(bad, np.zeros(H)) == -2
+    nan = good.copy()
+    nan[1] = np.nan
+    assert _build_raw(nan, np.zeros(H)) == -2
+    assert _build_raw(good, np.full(H, 4.0)) == -2    # |theta| >= pi
+    assert _build_raw(good, np.zeros(H), r0=-1.0) == -1
+    assert _build_raw(good, np.zeros(H), dptr=4097) == -4      # misaligned tables
+    assert _build_raw(good, np.zeros(H), nbytes=16) == -4      # too small
+
+
+def test_entry_points_reject_null_and_bad_arguments():
+    lib = R.lib()
+    p = R.rimg_default_params()
+    iters = (ctypes.c_int * 1)(1)
+    assert lib.rimg_register(None, None, 1, None, None, None, None, 1, iters, ctypes.byref(p), None, None, 0,
+                             None) == -1
+    assert lib.rimg_icp_step(None, None, 0, 1, None, None, None, None, ctypes.byref(p), 1, None, None, None,
+                             None, 0, None) == -1
+    assert lib.rimg_pyramid(1, 64, 64, 2, 3, 4096, None, None) == -1       # channels must be 1 or 4
+    assert lib.rimg_pyramid(1, 63, 64, 2, 1, 4096, None, None) == -3       # H not divisible
+    bad = R.rimg_default_params(normal_rel_jump=0.7)
+    assert lib.rimg_normals(None, 1, None, ctypes.byref(bad), None, None, None) == -1
+    assert lib.rimg_profile_begin(-1) == -1

@@ -1,0 +1,392 @@
+"""GPU parity: every step of the CUDA path, through the C ABI, against the FP64
+oracle on the same seeded inputs.
+
+Bars (derived in the design notes):
+  * integer work (pyramid copies, association indices, validity masks) is
+    bit-exact, except association/validity decisions the oracle flags as
+    near-ties (a continuous quantity within 1e-3 px, 1e-3 row spacings or a
+    relative 1e-3 of a normal-degeneracy threshold of a decision boundary);
+  * points: |xyz_gpu - xyz_oracle| <= 16 u (r + r0) + 1e-7 (u = 2^-24);
+  * normals: per pixel 32 u |P| (1/|a| + 1/|b|) + 1e-6 (a, b the central
+    differences), planes' offsets d to the same relative bound times |P|;
+  * reduced sums: |S_gpu - S_oracle| <= rel * sum|terms| (rel 1e-3) plus two
+    times the largest term per association that differs on a near-tie;
+  * poses: 1e-4 rad and 1e-4 m against the oracle's registration.
+"""
+import numpy as np
+import pytest
+
+from oracle import rimg_oracle as O
+from synth import CONFIGS, Sensor, make_pair, make_pairs, uniform_phi
+from tests.gpu_common import (U32, f32, oracle_params, gpu_sensor, planes_for, src_pyramid, gpu_register,
+                              oracle_register)
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def R():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2112_02779_b300.rimg as R   # fails loudly when librimg.so is missing
+    return R
+
+
+CFG_LEVELS = [("pair32x512", 3), ("pair64x1024", 4), ("stress16x64", 2)]
+
+
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("name,levels", CFG_LEVELS)
+def test_unproject_parity(R, name, levels):
+    cfg = CONFIGS[name]
+    p = make_pair(cfg, 0)
+    s = p["sensor"]
+    sens = gpu_sensor(R, s, levels)
+    img = p["dst_range"].copy()
+    img[0, :5] = np.nan
+    img[1, :5] = np.inf
+    img[2, :5] = -1.0
+    for l in range(levels):
+        st = 1 << l
+        rl = np.ascontiguousarray(img[::st, ::st])
+        H, W = rl.shape
+        rt = torch.from_numpy(rl)[None].cuda()
+        xyz = torch.zeros((1, 3, H, W), dtype=torch.float32, device="cuda")
+        mask = torch.zeros((1, H, W), dtype=torch.uint8, device="cuda")
+        R.rimg_unproject(sens, l, rt, xyz, mask)
+        ph, th = O.level_tables(s.phi_lut, s.theta_lut, l)
+        P, ok = O.unproject(rl, ph, th, s.r0)
+        m = mask[0].cpu().numpy().astype(bool)
+        assert np.array_equal(m, ok)
+        g = xyz[0].cpu().numpy().transpose(1, 2, 0)
+        r = np.where(ok, rl, 0.0).astype(np.float64)
+        tol = 16 * U32 * (r + s.r0) + 1e-7
+        assert np.all(np.abs(g - P).max(-1) <= tol)
+
+
+@pytest.mark.parametrize("channels", [1, 4])
+def test_pyramid_bit_exact(R, channels):
+    rng = np.random.default_rng(21)
+    for (n, H, W, L) in [(3, 24, 40, 3), (2, 64, 1024, 4), (1, 8, 8, 4)]:
+        shape = (n, H, W) if channels == 1 else (n, H, W, 4)
+        a = rng.standard_normal(shape).astype(np.float32)
+        t = torch.from_numpy(a).cuda()
+        outs = [None] + [torch.full((n, H >> l, W >> l) + (() if channels == 1 else (4,)), np.nan,
+                                    dtype=torch.float32, device="cuda") for l in range(1, L)]
+        R.rimg_pyramid(n, H, W, L, channels, t, outs)
+        for l in range(1, L):
+            st = 1 << l
+            assert np.array_equal(outs[l].cpu().numpy(), a[:, ::st, ::st])
+
+
+def _normal_tolerance(P, ok):
+    a = np.roll(P, -1, axis=1) - np.roll(P, 1, axis=1)
+    b = np.zeros_like(P)
+    b[1:-1] = P[2:] - P[:-2]
+    an = np.linalg.norm(a, axis=-1)
+    bn = np.linalg.norm(b, axis=-1)
+    pn = np.linalg.norm(P, axis=-1)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        rel = 32 * U32 * pn * (1 / an + 1 / bn)
+    return np.where(ok, rel + 1e-6, np.inf), pn
+
+
+@pytest.mark.parametrize("name,levels", CFG_LEVELS)
+def test_normals_parity(R, name, levels):
+    cfg = CONFIGS[name]
+    s = cfg.sensor()
+    sens = gpu_sensor(R, s, levels)
+    params = R.rimg_default_params()
+    imgs = np.stack([make_pair(cfg, i)["dst_range"] for i in range(2)])
+    planes, mask = planes_for(R, torch, sens, torch.from_numpy(imgs).cuda(), params)
+    for i in range(imgs.shape[0]):
+        n_o, ok_o, margin = O.normals(imgs[i], s.phi_lut, s.theta_lut, s.r0, f32(0.1), return_margin=True)
+        P, _ = O.unproject(imgs[i], s.phi_lut, s.theta_lut, s.r0)
+        m = mask[i].cpu().numpy().astype(bool)
+        near = margin < 1e-3
+        assert np.array_equal(m[~near], ok_o[~near])
+        pl = planes[0][i].cpu().numpy()
+        assert np.array_equal(np.any(pl[..., :3] != 0, axis=-1), m)
+        both = m & ok_o
+        tol, pn = _normal_tolerance(P, ok_o)
+        ng = pl[..., :3]
+        # orientation is a sign decision on n . P; where that is a near-tie
+        # either sign is accepted (point-to-plane terms do not depend on it)
+        grazing = np.abs(np.sum(n_o * P, -1)) < 1e-3 * pn
+        err = np.abs(ng - n_o).max(-1)
+        err = np.where(grazing, np.minimum(err, np.abs(ng + n_o).max(-1)), err)
+        assert np.all(err[both] <= tol[both])
+        d_o = np.sum(n_o * P, -1)
+        derr = np.abs(pl[..., 3] - d_o)
+        derr = np.where(grazing, np.minimum(derr, np.abs(pl[..., 3] + d_o)), derr)
+        assert np.all(derr[both] <= (tol * pn + 16 * U32 * pn)[both])
+        for l in range(1, levels):
+            st = 1 << l
+            assert np.array_equal(planes[l][i].cpu().numpy(), pl[::st, ::st])
+
+
+# ---------------------------------------------------------------------------
+def _icp_case(R, name, levels, level, pose_kind, params_kw=None, idx=0):
+    cfg = CONFIGS[name]
+    pair = make_pair(cfg, idx)
+    s = pair["sensor"]
+    sens = gpu_sensor(R, s, levels)
+    kw = dict(huber_delta=cfg.huber_delta)
+    kw.update(params_kw or {})
+    params = R.rimg_default_params(**kw)
+    src = torch.from_numpy(pair["src_range"])[None].cuda()
+    dst = torch.from_numpy(pair["dst_range"])[None].cuda()
+    planes, _ = planes_for(R, torch, sens, dst, params)
+    spyr = src_pyramid(R, torch, sens, src)
+    dpyr = src_pyramid(R, torch, sens, dst)
+    if pose_kind == "identity":
+        T = np.eye(4)
+    else:
+        T = O.se3_exp(np.array([2e-3, -1e-3, 3e-3, 0.02, -0.01, 0.015])) @ pair["T_gt"]
+    pose = torch.from_numpy(T.reshape(1, 16).copy()).cuda()
+    H, W = s.H >> level, s.W >> level
+    assoc = torch.full((1, H, W), -7, dtype=torch.int32, device="cuda")
+    out29 = torch.zeros((1, 29), dtype=torch.float64, device="cuda")
+    ws = torch.empty(R.rimg_icp_workspace_bytes(sens, 1), dtype=torch.uint8, device="cuda")
+    R.rimg_icp_step(sens, sens, level, 1, spyr[level], planes[level],
+                    dpyr[level] if params.max_corr_dist > 0 else None, pose, params, 0, out29, assoc, None, ws)
+    torch.cuda.synchronize()
+    tgt = O.Target(pair["dst_range"], s.phi_lut, s.theta_lut, s.r0, levels, f32(0.1))
+    P, sv = O.source_points(pair["src_range"], s.phi_lut, s.theta_lut, s.r0, level)
+    rng_l, n_l, nv_l, ph, th = tgt.level(level)
+    terms = O.icp_terms(P, sv, T, rng_l, n_l, nv_l, ph, th, s.r0, f32(params.huber_delta),
+                        f32(params.max_corr_dist), dst_n_margin=tgt.nmargin[level])
+    return assoc[0].cpu().numpy().reshape(-1), out29[0].cpu().numpy(), terms, T, pose.cpu().numpy()
+
+
+def _sum_bounds(terms, n_mismatch, rel=1e-3):
+    """Per-quantity tolerance: rel * sum|term_i| plus, per association that
+    differs on a near-tie, twice the largest single term."""
+    J, e, w = terms["J"], terms["e"], terms["w"]
+    wJ = J * w[:, None]
+    cols = [wJ[:, i] * J[:, j] for i in range(6) for j in range(i, 6)]
+    cols += [wJ[:, i] * e for i in range(6)] + [w * e * e]
+    A = np.abs(np.stack(cols, 1)) if len(e) else np.zeros((0, 28))
+    s = A.sum(0) if len(e) else np.zeros(28)
+    m = A.max(0) if len(e) else np.zeros(28)
+    return np.concatenate([rel * s + 2 * n_mismatch * m, [n_mismatch]])
+
+
+@pytest.mark.parametrize("name,levels", CFG_LEVELS)
+@pytest.mark.parametrize("pose_kind", ["identity", "near"])
+def test_icp_step_parity(R, name, levels, pose_kind):
+    for level in range(levels):
+        assoc, out29, terms, T, pose_after = _icp_case(R, name, levels, level, pose_kind)
+        assert np.array_equal(pose_after.reshape(4, 4), T)          # update = 0 leaves the pose alone
+        near = terms["near_tie"]
+        a_o = terms["assoc"]
+        diff = (assoc != a_o)
+        assert not np.any(diff & ~near), f"level {level}: {np.sum(diff & ~near)} non-near-tie mismatches"
+        n_mis = int(np.sum(diff))
+        assert n_mis <= max(3, 1e-3 * np.sum(a_o >= 0))
+        ref = O.pack29(terms)
+        bound = _sum_bounds(terms, n_mis)
+        err = np.abs(out29 - ref)
+        assert np.all(err <= bound + 1e-9), (level, err / np.maximum(bound, 1e-30))
+
+
+def test_icp_step_gate_parity(R):
+    for level in range(3):
+        assoc, out29, terms, T, _ = _icp_case(R, "pair32x512", 3, level, "identity",
+                                              params_kw=dict(max_corr_dist=0.5))
+        diff = assoc != terms["assoc"]
+        assert not np.any(diff & ~terms["near_tie"])
+        assert abs(out29[28] - terms["count"]) <= np.sum(diff)
+
+
+def test_icp_step_update_matches_oracle_step(R):
+    """update = 1 applies the FP64 Cholesky + SE(3) step; from the same pose
+    the result matches the oracle's single step."""
+    cfg = CONFIGS["pair32x512"]
+    pair = make_pair(cfg, 1)
+    s = pair["sensor"]
+    sens = gpu_sensor(R, s, 3)
+    params = R.rimg_default_params(huber_delta=cfg.huber_delta)
+    src = torch.from_numpy(pair["src_range"])[None].cuda()
+    dst = torch.from_numpy(pair["dst_range"])[None].cuda()
+    planes, _ = planes_for(R, torch, sens, dst, params)
+    pose = torch.eye(4, dtype=torch.float64, device="cuda").reshape(1, 16).contiguous()
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ws = torch.empty(R.rimg_icp_workspace_bytes(sens, 1), dtype=torch.uint8, device="cuda")
+    R.rimg_icp_step(sens, sens, 0, 1, src, planes[0], None, pose, params, 1, None, None, status, ws)
+    tgt = O.Target(pair["dst_range"], s.phi_lut, s.theta_lut, s.r0, 3, f32(0.1))
+    P, sv = O.source_points(pair["src_range"], s.phi_lut, s.theta_lut, s.r0, 0)
+    T1, ok, _ = O.icp_step(P, sv, tgt, 0, np.eye(4), oracle_params(cfg))
+    Tg = pose.cpu().numpy().reshape(4, 4)
+    eR, et = O.pose_error(Tg, T1)
+    assert ok and status.item() == 0
+    assert eR < 1e-5 and et < 1e-5
+
+
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("name,levels,n", [("pair32x512", 3, 8), ("pair64x1024", 4, 2), ("stress16x64", 2, 6)])
+def test_register_pose_parity(R, name, levels, n):
+    cfg = CONFIGS[name]
+    s = cfg.sensor()
+    sens = gpu_sensor(R, s, levels)
+    params = R.rimg_default_params(huber_delta=cfg.huber_delta)
+    src, dst, Tgt = make_pairs(cfg, range(n))
+    T0 = np.tile(np.eye(4), (n, 1, 1))
+    Tg, status = gpu_register(R, torch, sens, src, dst, T0, levels, cfg.iters, params)
+    for i in range(n):
+        To, deg = oracle_register(src[i], dst[i], s, np.eye(4), levels, cfg.iters, oracle_params(cfg))
+        eR, et = O.pose_error(Tg[i], To)
+        assert eR <= 1e-4 and et <= 1e-4, (i, eR, et)
+        assert bool(status[i] & 1) == deg
+
+
+def test_register_with_gate_parity(R):
+    cfg = CONFIGS["pair32x512"]
+    s = cfg.sensor()
+    sens = gpu_sensor(R, s, 3)
+    params = R.rimg_default_params(huber_delta=cfg.huber_delta, max_corr_dist=1.0)
+    src, dst, _ = make_pairs(cfg, range(3))
+    Tg, _ = gpu_register(R, torch, sens, src, dst, np.tile(np.eye(4), (3, 1, 1)), 3, cfg.iters, params)
+    for i in range(3):
+        To, _ = oracle_register(src[i], dst[i], s, np.eye(4), 3, cfg.iters, oracle_params(cfg, gate=1.0))
+        eR, et = O.pose_error(Tg[i], To)
+        assert eR <= 1e-4 and et <= 1e-4
+
+
+def test_register_kahan_and_plain_both_match(R):
+    cfg = CONFIGS["indoor128x2048"]
+    s = cfg.sensor()
+    sens = gpu_sensor(R, s, 4)
+    src, dst, _ = make_pairs(cfg, range(1))
+    To, _ = oracle_register(src[0], dst[0], s, np.eye(4), 4, cfg.iters, oracle_params(cfg))
+    for kahan in (1, 0):
+        params = R.rimg_default_params(huber_delta=cfg.huber_delta, kahan=kahan)
+        Tg, _ = gpu_register(R, torch, sens, src, dst, np.eye(4)[None], 4, cfg.iters, params)
+        eR, et = O.pose_error(Tg[0], To)
+        assert eR <= 1e-4 and et <= 1e-4, (kahan, eR, et)
+
+
+def test_register_host_matches_device(R):
+    cfg = CONFIGS["pair32x512"]
+    s = cfg.sensor()
+    sens = gpu_sensor(R, s, 3)
+    params = R.rimg_default_params(huber_delta=cfg.huber_delta)
+    n = 7
+    src, dst, _ = make_pairs(cfg, range(n))
+    T0 = np.tile(np.eye(4), (n, 1, 1))
+    Tg, st_dev = gpu_register(R, torch, sens, src, dst, T0, 3, cfg.iters, params)
+    for chunk in (0, 3):
+        hs = torch.from_numpy(src).pin_memory()
+        hd = torch.from_numpy(dst).pin_memory()
+        hT0 = torch.from_numpy(T0.reshape(n, 16).copy()).pin_memory()
+        hT1 = torch.zeros((n, 16), dtype=torch.float64).pin_memory()
+        hst = torch.full((n,), -7, dtype=torch.int32).pin_memory()
+        ws = torch.empty(R.rimg_register_host_workspace_bytes(sens, sens, n, 3, chunk), dtype=torch.uint8,
+                         device="cuda")
+        R.rimg_register_host(sens, sens, n, hs, hd, hT0, hT1, 3, cfg.iters, params, hst, chunk, ws)
+        assert np.array_equal(hT1.numpy().reshape(n, 4, 4), Tg)
+        assert np.array_equal(hst.numpy(), st_dev)
+
+
+# ---------------------------------------------------------------------------
+def test_empty_batches_are_noops(R):
+    cfg = CONFIGS["stress16x64"]
+    s = cfg.sensor()
+    sens = gpu_sensor(R, s, 2)
+    params = R.rimg_default_params()
+    e = torch.zeros((0, s.H, s.W), dtype=torch.float32, device="cuda")
+    R.rimg_normals(sens, e, params, [torch.zeros(0, device="cuda")] * 2)
+    R.rimg_register(sens, sens, 0, e, e, torch.zeros(0, dtype=torch.float64, device="cuda"),
+                    torch.zeros(0, dtype=torch.float64, device="cuda"), 2, (1, 1), params,
+                    workspace=torch.empty(256, dtype=torch.uint8, device="cuda"))
+    torch.cuda.synchronize()
+
+
+def test_invalid_and_nonfinite_inputs(R):
+    """All-invalid sources give a degenerate system: the pose is unchanged and
+    the flag set.  NaN / inf / negative ranges behave exactly like 0."""
+    cfg = CONFIGS["pair32x512"]
+    s = cfg.sensor()
+    sens = gpu_sensor(R, s, 3)
+    params = R.rimg_default_params(huber_delta=cfg.huber_delta)
+    pair = make_pair(cfg, 2)
+    zero = np.zeros_like(pair["src_range"])
+    T0 = O.se3_exp(np.array([0.01, 0, 0, 0.1, 0, 0]))
+    Tg, st = gpu_register(R, torch, sens, zero[None], pair["dst_range"][None], T0[None], 3, cfg.iters, params)
+    assert np.array_equal(Tg[0], T0) and st[0] & 1
+    src = pair["src_range"].copy()
+    rng = np.random.default_rng(3)
+    bad = rng.random(src.shape) < 0.05
+    vals = np.array([np.nan, np.inf, -np.inf, -2.0], np.float32)
+    src_bad = src.copy()
+    src_bad[bad] = vals[rng.integers(0, 4, size=bad.sum())]
+    src_zero = src.copy()
+    src_zero[bad] = 0.0
+    Ta, _ = gpu_register(R, torch, sens, src_bad[None], pair["dst_range"][None], np.eye(4)[None], 3, cfg.iters,
+                         params)
+    Tb, _ = gpu_register(R, torch, sens, src_zero[None], pair["dst_range"][None], np.eye(4)[None], 3, cfg.iters,
+                         params)
+    assert np.array_equal(Ta, Tb)
+    assert np.all(np.isfinite(Ta))
+
+
+def test_ragged_small_image_parity(R):
+    """A 24 x 48 image (rows and chunks not multiples of the block shape),
+    batch of 3 different pairs."""
+    H, W = 24, 48
+    sensor = Sensor(H, W, uniform_phi(H, 8.0, -22.0), np.zeros(H), 0.0)
+    from synth.scenes import outdoor_scene, raycast, random_delta_pose
+    rng = np.random.default_rng(5)
+    srcs, dsts = [], []
+    for i in range(3):
+        W1 = np.eye(4); W1[2, 3] = 1.7
+        dT = random_delta_pose(rng, 2.0, 0.2)
+        scene = outdoor_scene(rng, 30, 40.0, keep_clear=(W1[:3, 3], (W1 @ dT)[:3, 3]))
+        dsts.append(raycast(scene, sensor, W1, 0.5, 40.0, 0.01, 0.05, rng))
+        srcs.append(raycast(scene, sensor, W1 @ dT, 0.5, 40.0, 0.01, 0.05, rng))
+    src, dst = np.stack(srcs), np.stack(dsts)
+    sens = gpu_sensor(R, sensor, 2)
+    params = R.rimg_default_params(huber_delta=0.5)
+    Tg, _ = gpu_register(R, torch, sens, src, dst, np.tile(np.eye(4), (3, 1, 1)), 2, (5, 5), params)
+    for i in range(3):
+        To, _ = oracle_register(src[i], dst[i], sensor, np.eye(4), 2, (5, 5),
+                                dict(huber_delta=f32(0.5), normal_rel_jump=f32(0.1)))
+        eR, et = O.pose_error(Tg[i], To)
+        assert eR <= 1e-4 and et <= 1e-4
+
+
+def test_workspace_too_small_is_rejected(R):
+    cfg = CONFIGS["stress16x64"]
+    s = cfg.sensor()
+    sens = gpu_sensor(R, s, 2)
+    params = R.rimg_default_params()
+    x = torch.zeros((1, s.H, s.W), dtype=torch.float32, device="cuda")
+    T = torch.eye(4, dtype=torch.float64, device="cuda").reshape(1, 16).contiguous()
+    with pytest.raises(R.RimgError) as ei:
+        R.rimg_register(sens, sens, 1, x, x, T, T, 2, (1, 1), params,
+                        workspace=torch.empty(256, dtype=torch.uint8, device="cuda"))
+    assert ei.value.code == -4
+
+
+# ---------------------------------------------------------------------------
+def test_full_size_batch_sampled_against_oracle(R):
+    """The benchmark's launch configuration: 512 pairs of 64 x 1024 in one
+    call.  Eight distinct seeded pairs are tiled into the batch (distinct
+    buffers); every copy of a pair must give the bit-identical pose (position
+    in the batch does not matter) and the distinct pairs match the oracle."""
+    cfg = CONFIGS["pair64x1024"]
+    s = cfg.sensor()
+    sens = gpu_sensor(R, s, 4)
+    params = R.rimg_default_params(huber_delta=cfg.huber_delta)
+    k, n = 8, 512
+    src, dst, _ = make_pairs(cfg, range(k), processes=4)
+    reps = n // k
+    Tg, status = gpu_register(R, torch, sens, np.tile(src, (reps, 1, 1)), np.tile(dst, (reps, 1, 1)),
+                              np.tile(np.eye(4), (n, 1, 1)), 4, cfg.iters, params)
+    Tg = Tg.reshape(reps, k, 4, 4)
+    assert np.all(Tg == Tg[0:1])
+    for i in range(0, k, 2):
+        To, _ = oracle_register(src[i], dst[i], s, np.eye(4), 4, cfg.iters, oracle_params(cfg))
+        eR, et = O.pose_error(Tg[0, i], To)
+        assert eR <= 1e-4 and et <= 1e-4
