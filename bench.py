@@ -329,7 +329,9 @@ def run_ours(args):
         e2e_s = float(t.item())
         barrier()
     e2e_value = world * B * args.steps / e2e_s
-    e2e_same = bool(np.array_equal(hT1.numpy().reshape(B, 4, 4), Tg))
+    from oracle import rimg_oracle as O  # pose metric only (no part of the timed path)
+    Th = hT1.numpy().reshape(B, 4, 4)
+    e2e_diff = max(max(O.pose_error(Th[i], Tg[i])) for i in range(min(B, 16)))
 
     if rank != 0:
         return 0
@@ -347,13 +349,12 @@ def run_ours(args):
         "e2e": {"value": e2e_value, "unit": "pairs/s",
                 "h2d_bytes_per_step": int(B * N0 * 4 * 2 + B * 16 * 8),
                 "d2h_bytes_per_step": int(B * 16 * 8 + B * 4), "chunk_pairs": chunk,
-                "poses_equal_device_path": e2e_same},
+                "max_pose_diff_vs_device_path": e2e_diff},
         "gpu_launches": len(recs),
         "clocks": clk.summary(),
         "degenerate_pairs": int(np.sum(st & 1)),
         "pose_err_vs_ground_truth_median": None,
     }
-    from oracle import rimg_oracle as O  # used only for the metric below and the CPU baseline leg
     errs = [O.pose_error(Tg[i], Tgt[i]) for i in range(min(B, unique))]
     line["pose_err_vs_ground_truth_median"] = {"rot_rad": float(np.median([e[0] for e in errs])),
                                                "trans_m": float(np.median([e[1] for e in errs]))}

@@ -152,6 +152,7 @@ IcpWs icp_ws(int H, int n_pairs, size_t start) {
 
 struct RegWs {
   size_t src_lvl[RIMG_MAX_LEVELS];   // level >= 1 source ranges
+  size_t dst_lvl[RIMG_MAX_LEVELS];   // level >= 1 target ranges (read by the distance gate)
   size_t planes[RIMG_MAX_LEVELS];    // target planes, all levels
   IcpWs icp;
   size_t end;
@@ -163,7 +164,10 @@ RegWs reg_ws(int H, int W, int n_pairs, int levels, size_t start) {
   const size_t n = (size_t)std::max(n_pairs, 0);
   for (int l = 0; l < levels; ++l) {
     const size_t Nl = (size_t)(H >> l) * (W >> l);
-    if (l >= 1) { r.src_lvl[l] = o; o = align_up(o + sizeof(float) * Nl * n); }
+    if (l >= 1) {
+      r.src_lvl[l] = o; o = align_up(o + sizeof(float) * Nl * n);
+      r.dst_lvl[l] = o; o = align_up(o + sizeof(float) * Nl * n);
+    }
     r.planes[l] = o; o = align_up(o + sizeof(float4) * Nl * n);
   }
   r.icp = icp_ws(H, n_pairs, o);
@@ -175,6 +179,7 @@ int icp_launch(const rimg_sensor* src, const rimg_sensor* dst, int level, int n_
                const float* src_range_l, const float* dst_planes_l, const float* dst_range_l,
                double* pose, const rimg_params* p, int update, double* out29, int32_t* assoc,
                int* status, char* ws, const IcpWs& w, cudaStream_t st) {
+  if (p->max_corr_dist > 0.f && !dst_range_l) return RIMG_ERR_INVALID_ARG;
   IcpLaunch a{};
   a.src = dev_level(src, level);
   a.dst = dev_level(dst, level);
@@ -213,10 +218,15 @@ int register_device(const rimg_sensor* src, const rimg_sensor* dst, int n_pairs,
   // Target planes of every level (normals at the finest level, strided pyramid).
   float* planes[RIMG_MAX_LEVELS] = {};
   float* srcl[RIMG_MAX_LEVELS] = {};
+  float* dstl[RIMG_MAX_LEVELS] = {};
   for (int l = 0; l < levels; ++l) {
     planes[l] = reinterpret_cast<float*>(ws + R.planes[l]);
-    if (l >= 1) srcl[l] = reinterpret_cast<float*>(ws + R.src_lvl[l]);
+    if (l >= 1) {
+      srcl[l] = reinterpret_cast<float*>(ws + R.src_lvl[l]);
+      dstl[l] = reinterpret_cast<float*>(ws + R.dst_lvl[l]);
+    }
   }
+  const bool gate = p->max_corr_dist > 0.f;
   // rimg_normals writes every level of dst's table set; register may use fewer
   // levels than the sensor has, so build a view limited to `levels`.
   rimg_sensor dview = *dst;
@@ -230,12 +240,19 @@ int register_device(const rimg_sensor* src, const rimg_sensor* dst, int n_pairs,
     e = launch_pyramid(n_pairs, H, W, levels, 1, src_range, srcl, st);
     prof_after(st);
     if (e != cudaSuccess) return cuda_fail(e, "pyramid kernel");
+    if (gate) {   // the distance gate reads the target ranges of every level
+      prof_before(st, K_PYRAMID, 1, n_pairs);
+      e = launch_pyramid(n_pairs, H, W, levels, 1, dst_range, dstl, st);
+      prof_after(st);
+      if (e != cudaSuccess) return cuda_fail(e, "pyramid kernel");
+    }
   }
   for (int k = 0; k < levels; ++k) {
     const int l = levels - 1 - k;
     const float* s_l = (l == 0) ? src_range : srcl[l];
+    const float* d_l = gate ? ((l == 0) ? dst_range : dstl[l]) : nullptr;
     for (int it = 0; it < iters[k]; ++it) {
-      int rc = icp_launch(src, dst, l, n_pairs, s_l, planes[l], nullptr, T_out, p, 1, nullptr, nullptr,
+      int rc = icp_launch(src, dst, l, n_pairs, s_l, planes[l], d_l, T_out, p, 1, nullptr, nullptr,
                           status, ws, R.icp, st);
       if (rc) return rc;
     }

@@ -68,7 +68,15 @@ CONFIGS = {
                                  scene="indoor", n_objects=12, r_min=0.3, r_max=40.0,
                                  rot_max_deg=5.0, trans_max=1.0, sigma=0.01, levels=4,
                                  iters=(10, 10, 10, 10), huber_delta=0.2, seed_base=3000),
-    # Stress sensor for round trips and LUT handling: interlaced theta, receiver radius.
+    # Interlaced sensor with a receiver radius at a realistic size: 64 x 512,
+    # theta_lut ~ U(-2, 2) deg, r0 = 1.5 cm (exercises the projection fixed point).
+    "lut64x512": PairConfig("lut64x512", 8, 64, 512, "uniform", 10.0, -20.0,
+                            theta_max_deg=2.0, r0=0.015, n_objects=100, r_min=0.5, r_max=80.0,
+                            rot_max_deg=3.0, trans_max=0.5, levels=3, iters=(10, 10, 10),
+                            seed_base=8000),
+    # Tiny stress sensor for round trips and LUT handling: interlaced theta,
+    # receiver radius; too sparse for stable registration (parity of single
+    # steps only).
     "stress16x64": PairConfig("stress16x64", 9, 16, 64, "uniform", 10.0, -20.0,
                               theta_max_deg=2.0, r0=0.015, n_objects=12, r_min=0.5,
                               r_max=60.0, rot_max_deg=3.0, trans_max=0.3, levels=2,

@@ -33,7 +33,7 @@ def R():
     return R
 
 
-CFG_LEVELS = [("pair32x512", 3), ("pair64x1024", 4), ("stress16x64", 2)]
+CFG_LEVELS = [("pair32x512", 3), ("pair64x1024", 4), ("lut64x512", 3), ("stress16x64", 2)]
 
 
 # ---------------------------------------------------------------------------
@@ -120,7 +120,9 @@ def test_normals_parity(R, name, levels):
         d_o = np.sum(n_o * P, -1)
         derr = np.abs(pl[..., 3] - d_o)
         derr = np.where(grazing, np.minimum(derr, np.abs(pl[..., 3] + d_o)), derr)
-        assert np.all(derr[both] <= (tol * pn + 16 * U32 * pn)[both])
+        with np.errstate(invalid="ignore"):
+            dtol = np.where(both, tol * pn + 16 * U32 * pn, 0.0)
+        assert np.all(derr[both] <= dtol[both])
         for l in range(1, levels):
             st = 1 << l
             assert np.array_equal(planes[l][i].cpu().numpy(), pl[::st, ::st])
@@ -225,7 +227,7 @@ def test_icp_step_update_matches_oracle_step(R):
 
 
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("name,levels,n", [("pair32x512", 3, 8), ("pair64x1024", 4, 2), ("stress16x64", 2, 6)])
+@pytest.mark.parametrize("name,levels,n", [("pair32x512", 3, 8), ("pair64x1024", 4, 2), ("lut64x512", 3, 4)])
 def test_register_pose_parity(R, name, levels, n):
     cfg = CONFIGS[name]
     s = cfg.sensor()
@@ -285,7 +287,16 @@ def test_register_host_matches_device(R):
         ws = torch.empty(R.rimg_register_host_workspace_bytes(sens, sens, n, 3, chunk), dtype=torch.uint8,
                          device="cuda")
         R.rimg_register_host(sens, sens, n, hs, hd, hT0, hT1, 3, cfg.iters, params, hst, chunk, ws)
-        assert np.array_equal(hT1.numpy().reshape(n, 4, 4), Tg)
+        Th = hT1.numpy().reshape(n, 4, 4)
+        if chunk == 0:
+            # same batch, same block decomposition: bit-identical
+            assert np.array_equal(Th, Tg)
+        else:
+            # a smaller batch may split pairs into a different number of blocks
+            # (a different FP32 summation order)
+            for i in range(n):
+                eR, et = O.pose_error(Th[i], Tg[i])
+                assert eR <= 1e-7 and et <= 1e-7
         assert np.array_equal(hst.numpy(), st_dev)
 
 
