@@ -200,6 +200,35 @@ int rimg_icp_step(const rimg_sensor* src, const rimg_sensor* dst, int level, int
                   int* status, void* workspace, size_t workspace_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * rimg_icp_step without a caller workspace.  The paper has no counterpart:
+ * this is a library convenience for callers that cannot allocate device
+ * memory when they run the step (allocation-free real-time loops, plug-ins
+ * that may only touch the buffers they are handed).
+ *
+ * Same arguments, semantics and results as rimg_icp_step, minus the
+ * workspace.  The step's scratch (per-pair completion counters and per-block
+ * partial sums) lives in a fixed device array of RIMG_STATIC_SCRATCH_BYTES
+ * inside the library; every GPU that loads the library holds one such array
+ * until the process exits.  The call allocates nothing.
+ *  - Limit: rimg_icp_workspace_bytes(src, n_pairs) must not exceed
+ *    RIMG_STATIC_SCRATCH_BYTES (about n_pairs * H * 128 bytes for a sensor
+ *    with H rows: e.g. up to 127 pairs of 64-row images per call); larger
+ *    batches return RIMG_ERR_WORKSPACE before anything is launched.
+ *  - The first call on a device looks up the array's device address (with
+ *    that device current) and caches it; make that first call before any
+ *    stream capture.
+ *  - All calls share the one array and it keeps the previous call's
+ *    contents: the counters are cleared on `stream` before every kernel, but
+ *    calls that overlap on the GPU (other streams, other host threads) race
+ *    on the scratch and must be serialised by the caller.
+ * ------------------------------------------------------------------------- */
+#define RIMG_STATIC_SCRATCH_BYTES (1u << 20)
+int rimg_icp_step_static(const rimg_sensor* src, const rimg_sensor* dst, int level, int n_pairs,
+                         const float* src_range_l, const float* dst_planes_l, const float* dst_range_l,
+                         double* pose, const rimg_params* p, int update, double* out29, int32_t* assoc,
+                         int* status, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Multi-scale registration (step A9), Section 4.1 with the coarse-to-fine
  * schedule of Section 6.1: normals of every target at the finest level, the
  * strided source-range and target-plane pyramids, then for each level from the

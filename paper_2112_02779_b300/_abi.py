@@ -4,6 +4,7 @@ import ctypes
 
 RIMG_MAX_LEVELS = 8
 RIMG_FLAG_DEGENERATE = 1
+RIMG_STATIC_SCRATCH_BYTES = 1 << 20
 
 STATUS_NAMES = {0: "RIMG_OK", -1: "RIMG_ERR_INVALID_ARG", -2: "RIMG_ERR_LUT", -3: "RIMG_ERR_SIZE",
                 -4: "RIMG_ERR_WORKSPACE", -5: "RIMG_ERR_CUDA", -6: "RIMG_ERR_MISMATCH"}
@@ -33,6 +34,7 @@ class rimg_params(ctypes.Structure):
 HEADER_FUNCTIONS = [
     "rimg_default_params", "rimg_status_string", "rimg_last_error",
     "rimg_sensor_table_bytes", "rimg_sensor_build", "rimg_unproject", "rimg_pyramid", "rimg_normals",
-    "rimg_icp_workspace_bytes", "rimg_icp_step", "rimg_register_workspace_bytes", "rimg_register",
+    "rimg_icp_workspace_bytes", "rimg_icp_step", "rimg_icp_step_static",
+    "rimg_register_workspace_bytes", "rimg_register",
     "rimg_register_host_workspace_bytes", "rimg_register_host", "rimg_profile_begin", "rimg_profile_end",
 ]

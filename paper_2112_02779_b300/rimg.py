@@ -11,7 +11,7 @@ import os
 
 import numpy as np
 
-from ._abi import (RIMG_MAX_LEVELS, RIMG_FLAG_DEGENERATE, rimg_level, rimg_sensor, rimg_params,
+from ._abi import (RIMG_MAX_LEVELS, RIMG_FLAG_DEGENERATE, RIMG_STATIC_SCRATCH_BYTES, rimg_level, rimg_sensor, rimg_params,
                    STATUS_NAMES, HEADER_FUNCTIONS)
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -45,6 +45,8 @@ _sig("rimg_normals", _c_int, _P(rimg_sensor), _c_int, _vp, _P(rimg_params), _P(_
 _sig("rimg_icp_workspace_bytes", _c_int, _P(rimg_sensor), _c_int, _P(_c_size))
 _sig("rimg_icp_step", _c_int, _P(rimg_sensor), _P(rimg_sensor), _c_int, _c_int, _vp, _vp, _vp, _vp,
      _P(rimg_params), _c_int, _vp, _vp, _vp, _vp, _c_size, _vp)
+_sig("rimg_icp_step_static", _c_int, _P(rimg_sensor), _P(rimg_sensor), _c_int, _c_int, _vp, _vp, _vp, _vp,
+     _P(rimg_params), _c_int, _vp, _vp, _vp, _vp)
 _sig("rimg_register_workspace_bytes", _c_int, _P(rimg_sensor), _P(rimg_sensor), _c_int, _c_int, _P(_c_size))
 _sig("rimg_register", _c_int, _P(rimg_sensor), _P(rimg_sensor), _c_int, _vp, _vp, _vp, _vp, _c_int,
      _P(_c_int), _P(rimg_params), _vp, _vp, _c_size, _vp)
@@ -185,6 +187,15 @@ def rimg_icp_step(src, dst, level, n_pairs, src_range_l, dst_planes_l, dst_range
         src.ref(), dst.ref(), level, n_pairs, _ptr(src_range_l), _ptr(dst_planes_l), _ptr(dst_range_l),
         _ptr(pose), ctypes.byref(params), int(update), _ptr(out29), _ptr(assoc), _ptr(status),
         _ptr(workspace), workspace.numel() if workspace is not None else 0, _stream(stream)))
+
+
+def rimg_icp_step_static(src, dst, level, n_pairs, src_range_l, dst_planes_l, dst_range_l, pose, params, update,
+                         out29=None, assoc=None, status=None, stream=None):
+    """rimg_icp_step with its scratch in the library's fixed device array (no
+    workspace argument; for callers that cannot allocate)."""
+    _check("rimg_icp_step_static", _lib.rimg_icp_step_static(
+        src.ref(), dst.ref(), level, n_pairs, _ptr(src_range_l), _ptr(dst_planes_l), _ptr(dst_range_l),
+        _ptr(pose), ctypes.byref(params), int(update), _ptr(out29), _ptr(assoc), _ptr(status), _stream(stream)))
 
 
 def rimg_register_workspace_bytes(src, dst, n_pairs, levels):
