@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-pairs", type=int, default=8)
     ap.add_argument("--e2e-chunk", type=int, default=128)
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     return ap.parse_args()
 
 
@@ -139,6 +140,12 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def pose_error(T, T_ref):
+    """Rotation (rad, trace form) and translation (m) difference of two poses."""
+    c = np.clip((np.trace(T[:3, :3] @ T_ref[:3, :3].T) - 1.0) / 2.0, -1.0, 1.0)
+    return float(np.arccos(c)), float(np.linalg.norm(T[:3, 3] - T_ref[:3, 3]))
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     for f in ("kernel_icp.cu", "rimg_device.cuh", "rimg_internal.h"):
@@ -223,6 +230,43 @@ def run_reference(args):
     return 0
 
 
+def run_e2e(args, R, sens, params, cfg, src_np, dst_np, Tg, B, stream, dev, world, barrier):
+    """End to end through the host-buffer entry point: pinned host inputs, the
+    chunked H2D copies, registration and the D2H of poses all inside the timed
+    region."""
+    import torch
+    N0 = cfg.H * cfg.W
+    hs = torch.from_numpy(src_np).pin_memory()
+    hd = torch.from_numpy(dst_np).pin_memory()
+    hT0 = torch.eye(4, dtype=torch.float64).reshape(1, 16).repeat(B, 1).contiguous().pin_memory()
+    hT1 = torch.zeros((B, 16), dtype=torch.float64).pin_memory()
+    hst = torch.zeros(B, dtype=torch.int32).pin_memory()
+    chunk = min(args.e2e_chunk, B)
+    ws_h = torch.empty(R.rimg_register_host_workspace_bytes(sens, sens, B, cfg.levels, chunk), dtype=torch.uint8,
+                       device=dev)
+    for _ in range(2):
+        R.rimg_register_host(sens, sens, B, hs, hd, hT0, hT1, cfg.levels, cfg.iters, params, hst, chunk, ws_h,
+                             stream)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        R.rimg_register_host(sens, sens, B, hs, hd, hT0, hT1, cfg.levels, cfg.iters, params, hst, chunk, ws_h,
+                             stream)
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_s], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+        barrier()
+    Th = hT1.numpy().reshape(B, 4, 4)
+    diff = max(max(pose_error(Th[i], Tg[i])) for i in range(min(B, 16)))
+    return {"value": world * B * args.steps / e2e_s, "unit": "pairs/s",
+            "h2d_bytes_per_step": int(B * N0 * 4 * 2 + B * 16 * 8),
+            "d2h_bytes_per_step": int(B * 16 * 8 + B * 4), "chunk_pairs": chunk,
+            "max_pose_diff_vs_device_path": diff}
+
+
 def run_ours(args):
     rank, world, local = dist_env()
     import torch
@@ -303,36 +347,10 @@ def run_ours(args):
     Tg = T1.cpu().numpy().reshape(B, 4, 4)
     st = status.cpu().numpy()
 
-    # end to end through the host-buffer entry point (pinned host memory)
-    hs = torch.from_numpy(src_np).pin_memory()
-    hd = torch.from_numpy(dst_np).pin_memory()
-    hT0 = torch.eye(4, dtype=torch.float64).reshape(1, 16).repeat(B, 1).contiguous().pin_memory()
-    hT1 = torch.zeros((B, 16), dtype=torch.float64).pin_memory()
-    hst = torch.zeros(B, dtype=torch.int32).pin_memory()
-    chunk = min(args.e2e_chunk, B)
-    ws_h = torch.empty(R.rimg_register_host_workspace_bytes(sens, sens, B, cfg.levels, chunk), dtype=torch.uint8,
-                       device=dev)
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, R, sens, params, cfg, src_np, dst_np, Tg, B, stream, dev, world, barrier)
     del ws
-    for _ in range(2):
-        R.rimg_register_host(sens, sens, B, hs, hd, hT0, hT1, cfg.levels, cfg.iters, params, hst, chunk, ws_h,
-                             stream)
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        R.rimg_register_host(sens, sens, B, hs, hd, hT0, hT1, cfg.levels, cfg.iters, params, hst, chunk, ws_h,
-                             stream)
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_s], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-        barrier()
-    e2e_value = world * B * args.steps / e2e_s
-    from oracle import rimg_oracle as O  # pose metric only (no part of the timed path)
-    Th = hT1.numpy().reshape(B, 4, 4)
-    e2e_diff = max(max(O.pose_error(Th[i], Tg[i])) for i in range(min(B, 16)))
-
     if rank != 0:
         return 0
     line = {
@@ -346,22 +364,19 @@ def run_ours(args):
         "kernels": {f"{k[0]}@L{k[1]}": {"launches": len(v), "avg_ms": float(np.mean(v)),
                                         "share": float(sum(v) / all_total)} for k, v in sorted(per.items())},
         "icp_share_of_kernel_time": icp_total / all_total if all_total else None,
-        "e2e": {"value": e2e_value, "unit": "pairs/s",
-                "h2d_bytes_per_step": int(B * N0 * 4 * 2 + B * 16 * 8),
-                "d2h_bytes_per_step": int(B * 16 * 8 + B * 4), "chunk_pairs": chunk,
-                "max_pose_diff_vs_device_path": e2e_diff},
+        "e2e": e2e,
         "gpu_launches": len(recs),
         "clocks": clk.summary(),
         "degenerate_pairs": int(np.sum(st & 1)),
         "pose_err_vs_ground_truth_median": None,
     }
-    errs = [O.pose_error(Tg[i], Tgt[i]) for i in range(min(B, unique))]
+    errs = [pose_error(Tg[i], Tgt[i]) for i in range(min(B, unique))]
     line["pose_err_vs_ground_truth_median"] = {"rot_rad": float(np.median([e[0] for e in errs])),
                                                "trans_m": float(np.median([e[1] for e in errs]))}
     if not args.no_cpu_baseline and world == 1:
         n = min(args.cpu_sample_pairs, unique)
         v, dt, poses = cpu_oracle_sample(cfg, src_np, dst_np, n)
-        pe = [O.pose_error(Tg[i], poses[i]) for i in range(n)]
+        pe = [pose_error(Tg[i], poses[i]) for i in range(n)]
         line["cpu_baseline"] = {"value": v, "unit": "pairs/s", "cores": 1, "kind": "oracle",
                                 "sample": f"{n} pairs of the workload, FP64 numpy oracle, one host thread, "
                                           f"{dt:.1f} s",
