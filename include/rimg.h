@@ -54,17 +54,20 @@ typedef enum rimg_status {
  * callers treat it as read-only). */
 typedef struct rimg_level {
   int H, W;                 /* level size: H >> l, W >> l */
-  int n_bins;               /* entries of the inverse elevation table */
+  int n_bins;               /* entries of the inverse elevation table (<= 64 H) */
   int tie_up;               /* 1 when elevation decreases with the row index */
+  int bins_exact;           /* 1 when every bin holds at most one row boundary */
+  int has_theta;            /* 0 when theta_lut is identically zero */
   float s_lo, s_hi;         /* vertical field of view as sin(elevation) */
   float bin_scale;          /* n_bins / (s_hi - s_lo) */
   float w_over_2pi;         /* W / (2 pi) */
   size_t off_rows;          /* float4[H]: cos phi, sin phi, cos theta_lut, sin theta_lut */
-  size_t off_cols;          /* float2[W]: cos, sin of the column angle 2 pi u / W */
+  size_t off_cols;          /* float[W] cos, then (at off_cols + 4W) float[W] sin of 2 pi u / W */
   size_t off_thu;           /* float[H]:  theta_lut[v] * W / (2 pi) */
   size_t off_rank;          /* int[H]:    row of the j-th smallest elevation */
   size_t off_bnd;           /* float[H-1]: sin of the mid-elevation between ranks j, j+1 */
-  size_t off_bins;          /* int[n_bins]: rank at each bin's lower edge */
+  size_t off_bins;          /* int4[n_bins]: row below / row above the bin's boundary, the
+                               boundary (float bits, +inf if none), rank at the lower edge */
 } rimg_level;
 
 /* A sensor's intrinsics in device form: the elevation table phi_lut and the
@@ -105,8 +108,10 @@ const char* rimg_last_error(void);
  * theta_lut[H] (radians, HOST float64 arrays) come from the manufacturer.
  * The library precomputes, per pyramid level l (rows 2^l v of the finest
  * tables, W_l = W >> l), separable cos/sin tables for Eq. 1 and an inverse
- * elevation table (the 2H-entry table of Section 3.2, refined to the exact
- * Eq. 4 argmin by walking row boundaries).
+ * elevation table in sin(elevation) space (the inverse table of Section 3.2,
+ * sized so that each bin holds at most one row boundary, which makes one
+ * comparison give the exact Eq. 4 argmin; for tables too uneven for 64 H
+ * bins the device walks across the row boundaries instead).
  *
  * Requirements: levels in [1, RIMG_MAX_LEVELS]; H >> (levels-1) >= 2;
  * W divisible by 4 << (levels-1); phi_lut finite, strictly monotone, inside

@@ -12,7 +12,7 @@ STATUS_NAMES = {0: "RIMG_OK", -1: "RIMG_ERR_INVALID_ARG", -2: "RIMG_ERR_LUT", -3
 
 class rimg_level(ctypes.Structure):
     _fields_ = [("H", ctypes.c_int), ("W", ctypes.c_int), ("n_bins", ctypes.c_int), ("tie_up", ctypes.c_int),
-                ("s_lo", ctypes.c_float), ("s_hi", ctypes.c_float), ("bin_scale", ctypes.c_float),
+                ("bins_exact", ctypes.c_int), ("has_theta", ctypes.c_int), ("s_lo", ctypes.c_float), ("s_hi", ctypes.c_float), ("bin_scale", ctypes.c_float),
                 ("w_over_2pi", ctypes.c_float),
                 ("off_rows", ctypes.c_size_t), ("off_cols", ctypes.c_size_t), ("off_thu", ctypes.c_size_t),
                 ("off_rank", ctypes.c_size_t), ("off_bnd", ctypes.c_size_t), ("off_bins", ctypes.c_size_t)]

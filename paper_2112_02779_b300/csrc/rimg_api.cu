@@ -43,14 +43,14 @@ struct LevelLayout {
 
 LevelLayout level_layout(int Hl, int Wl, size_t start) {
   LevelLayout L{};
-  L.n_bins = 8 * Hl;
+  L.n_bins = 64 * Hl;           // capacity; rimg_sensor_build uses as many as the table needs
   size_t o = align_up(start);
   L.rows = o; o = align_up(o + sizeof(float4) * Hl);
-  L.cols = o; o = align_up(o + sizeof(float2) * Wl);
+  L.cols = o; o = align_up(o + sizeof(float) * 2 * Wl);   // cos[W] then sin[W]
   L.thu = o; o = align_up(o + sizeof(float) * Hl);
   L.rank = o; o = align_up(o + sizeof(int) * Hl);
   L.bnd = o; o = align_up(o + sizeof(float) * std::max(1, Hl - 1));
-  L.bins = o; o = align_up(o + sizeof(int) * L.n_bins);
+  L.bins = o; o = align_up(o + sizeof(int4) * L.n_bins);
   L.end = o;
   return L;
 }
@@ -116,15 +116,18 @@ DevLevel dev_level(const rimg_sensor* s, int l) {
   const char* base = static_cast<const char*>(s->d_tables);
   DevLevel d;
   d.rows = reinterpret_cast<const float4*>(base + L.off_rows);
-  d.cols = reinterpret_cast<const float2*>(base + L.off_cols);
+  d.cos_u = reinterpret_cast<const float*>(base + L.off_cols);
+  d.sin_u = reinterpret_cast<const float*>(base + L.off_cols + sizeof(float) * L.W);
   d.thu = reinterpret_cast<const float*>(base + L.off_thu);
   d.rank2row = reinterpret_cast<const int*>(base + L.off_rank);
   d.bnd = reinterpret_cast<const float*>(base + L.off_bnd);
-  d.bins = reinterpret_cast<const int*>(base + L.off_bins);
+  d.bins = reinterpret_cast<const int4*>(base + L.off_bins);
   d.H = L.H;
   d.W = L.W;
   d.n_bins = L.n_bins;
   d.tie_up = L.tie_up;
+  d.bins_exact = L.bins_exact;
+  d.has_theta = L.has_theta;
   d.s_lo = L.s_lo;
   d.s_hi = L.s_hi;
   d.bin_scale = L.bin_scale;
@@ -198,7 +201,7 @@ int icp_launch(const rimg_sensor* src, const rimg_sensor* dst, int level, int n_
   a.proj_iters = p->proj_iters;
   a.kahan = p->kahan;
   a.update = update;
-  icp_grid(a.src.H, a.src.W, n_pairs, &a.bpp, &a.rows_per_block);
+  icp_grid(a.src.H, a.src.W, n_pairs, &a.bpp, &a.rows_per_block, &a.threads);
   prof_before(st, K_ICP, level, n_pairs);
   cudaError_t e = launch_icp(a, st);
   prof_after(st);
@@ -366,19 +369,23 @@ int rimg_sensor_build(int H, int W, int levels, const double* phi_lut, const dou
       th[v] = theta_lut[v << l];
     }
     float4* rows = reinterpret_cast<float4*>(buf.data() + L.rows);
-    float2* cols = reinterpret_cast<float2*>(buf.data() + L.cols);
+    float* cosu = reinterpret_cast<float*>(buf.data() + L.cols);
+    float* sinu = cosu + Wl;
     float* thu = reinterpret_cast<float*>(buf.data() + L.thu);
     int* rank = reinterpret_cast<int*>(buf.data() + L.rank);
     float* bnd = reinterpret_cast<float*>(buf.data() + L.bnd);
-    int* bins = reinterpret_cast<int*>(buf.data() + L.bins);
+    int4* bins = reinterpret_cast<int4*>(buf.data() + L.bins);
+    bool any_theta = false;
     for (int v = 0; v < Hl; ++v) {
       rows[v] = make_float4((float)std::cos(ph[v]), (float)std::sin(ph[v]), (float)std::cos(th[v]),
                             (float)std::sin(th[v]));
       thu[v] = (float)(th[v] * Wl / (2.0 * kPi));
+      any_theta |= th[v] != 0.0;
     }
     for (int u = 0; u < Wl; ++u) {
       const double a = 2.0 * kPi * ((double)u / (double)Wl);
-      cols[u] = make_float2((float)std::cos(a), (float)std::sin(a));
+      cosu[u] = (float)std::cos(a);
+      sinu[u] = (float)std::sin(a);
     }
     // rank j = j-th smallest elevation
     std::vector<int> order(Hl);
@@ -395,18 +402,36 @@ int rimg_sensor_build(int H, int W, int levels, const double* phi_lut, const dou
     rimg_level& lv = s.level[l];
     lv.H = Hl;
     lv.W = Wl;
-    lv.n_bins = L.n_bins;
     lv.tie_up = desc ? 1 : 0;
+    lv.has_theta = any_theta ? 1 : 0;
     lv.s_lo = (float)std::sin(lo);
     lv.s_hi = (float)std::sin(hi);
-    lv.bin_scale = (float)((double)L.n_bins / ((double)lv.s_hi - (double)lv.s_lo));
     lv.w_over_2pi = (float)((double)Wl / (2.0 * kPi));
-    for (int b = 0; b < L.n_bins; ++b) {
-      const double edge = (double)lv.s_lo + (double)b / (double)lv.bin_scale;
-      int j = 0;
-      while (j < Hl - 1 && (double)bnd[j] < edge) ++j;
-      bins[b] = j;
+    // Bins narrower than the smallest gap between row boundaries hold at most
+    // one boundary each; then one comparison inside the bin decides the row.
+    const double range = (double)lv.s_hi - (double)lv.s_lo;
+    double min_gap = range;
+    for (int j = 0; j + 2 < Hl; ++j) min_gap = std::min(min_gap, (double)bnd[j + 1] - (double)bnd[j]);
+    long long nb = (min_gap > 0.0) ? (long long)std::ceil(range / min_gap) + 2 : (long long)L.n_bins;
+    nb = std::max<long long>(nb, 2LL * Hl);
+    nb = std::min<long long>(nb, (long long)L.n_bins);
+    lv.n_bins = (int)nb;
+    lv.bin_scale = (float)((double)nb / range);
+    bool exact = true;
+    for (int b = 0; b < lv.n_bins; ++b) {
+      const double e0 = (double)lv.s_lo + (double)b / (double)lv.bin_scale;
+      const double e1 = (double)lv.s_lo + (double)(b + 1) / (double)lv.bin_scale;
+      int j = 0;   // rank at the lower edge (ties follow the device's comparison)
+      while (j < Hl - 1 && (desc ? (double)bnd[j] <= e0 : (double)bnd[j] < e0)) ++j;
+      int inside = 0;
+      while (j + inside < Hl - 1 && (double)bnd[j + inside] < e1) ++inside;
+      if (inside > 1) exact = false;
+      float bb = (inside >= 1) ? bnd[j] : INFINITY;
+      int bits;
+      std::memcpy(&bits, &bb, sizeof(bits));
+      bins[b] = make_int4(rank[j], rank[std::min(j + 1, Hl - 1)], bits, j);
     }
+    lv.bins_exact = exact ? 1 : 0;
     lv.off_rows = L.rows;
     lv.off_cols = L.cols;
     lv.off_thu = L.thu;

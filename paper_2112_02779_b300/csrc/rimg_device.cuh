@@ -11,22 +11,29 @@ namespace rimg {
 // cos/sin(theta) = cos/sin(col + theta_lut) by the angle-addition identities.
 __device__ __forceinline__ float3 unproject_px(const DevLevel& L, int u, int v, float r) {
   const float4 rw = __ldg(L.rows + v);
-  const float2 cl = __ldg(L.cols + u);
-  const float ct = fmaf(cl.x, rw.z, -cl.y * rw.w);
-  const float st = fmaf(cl.y, rw.z, cl.x * rw.w);
+  const float cu = __ldg(L.cos_u + u), su = __ldg(L.sin_u + u);
+  const float ct = fmaf(cu, rw.z, -su * rw.w);
+  const float st = fmaf(su, rw.z, cu * rw.w);
   const float rc = r * rw.x;
-  return make_float3(fmaf(rc, ct, L.r0 * cl.x), fmaf(rc, st, L.r0 * cl.y), r * rw.y);
+  return make_float3(fmaf(rc, ct, L.r0 * cu), fmaf(rc, st, L.r0 * su), r * rw.y);
 }
 
 // Eq. 4 in sin(elevation) space: the row whose elevation is nearest to that
-// of a point with sin(elevation) = s.  The inverse table gives the rank at
-// the bin's lower edge; walking across the (sorted) mid-elevation boundaries
-// makes the result the exact argmin of the float tables.  Both walks are
-// bounded by H.
+// of a point with sin(elevation) = s.  Each bin of the inverse table holds at
+// most one mid-elevation boundary (bins_exact), so one comparison with it
+// picks the row below or above; the tie rule sends exact ties to the lower
+// row index.  For tables too uneven for that, the walk across the sorted
+// boundaries (bounded by H) gives the same argmin.
 __device__ __forceinline__ int row_from_sin(const DevLevel& L, float s) {
   int b = __float2int_rd((s - L.s_lo) * L.bin_scale);
   b = min(max(b, 0), L.n_bins - 1);
-  int j = __ldg(L.bins + b);
+  const int4 e = __ldg(L.bins + b);
+  if (L.bins_exact) {
+    const float bb = __int_as_float(e.z);
+    const bool above = L.tie_up ? (s >= bb) : (s > bb);
+    return above ? e.y : e.x;
+  }
+  int j = e.w;
   if (L.tie_up) {
     for (int k = 0; k < L.H && j < L.H - 1 && s >= __ldg(L.bnd + j); ++k) ++j;
     for (int k = 0; k < L.H && j > 0 && s < __ldg(L.bnd + j - 1); ++k) --j;
@@ -35,6 +42,30 @@ __device__ __forceinline__ int row_from_sin(const DevLevel& L, float s) {
     for (int k = 0; k < L.H && j > 0 && s <= __ldg(L.bnd + j - 1); ++k) --j;
   }
   return __ldg(L.rank2row + j);
+}
+
+// atan2(y, x) in (-pi, pi] from an odd polynomial of degree 15 for atan(t)
+// on t in [0, 1] (coefficients fitted here by iteratively re-weighted least
+// squares on Chebyshev nodes, i.e. close to minimax; max error 3.7e-8 rad in
+// exact arithmetic, 1.3e-7 rad evaluated in FP32) and the octant symmetries
+// atan(t) = pi/2 - atan(1/t), atan2(y, -x) = pi - atan2(y, x).
+__device__ __forceinline__ float atan2_poly(float y, float x) {
+  const float ax = fabsf(x), ay = fabsf(y);
+  const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
+  const float t = __fdividef(mn, mx);
+  const float t2 = t * t;
+  float p = -0.004054551851790431f;
+  p = fmaf(p, t2, 0.021862905109892965f);
+  p = fmaf(p, t2, -0.05591225506199317f);
+  p = fmaf(p, t2, 0.096421924387434f);
+  p = fmaf(p, t2, -0.13908627803290416f);
+  p = fmaf(p, t2, 0.19946565342346506f);
+  p = fmaf(p, t2, -0.3332986076193729f);
+  p = fmaf(p, t2, 0.999999335574615f);
+  float r = p * t;
+  r = (ay > ax) ? 1.57079632679489662f - r : r;
+  r = (x < 0.f) ? 3.14159265358979324f - r : r;
+  return copysignf(r, y);
 }
 
 // Column from the continuous estimate u_c: floor(u_c + 1/2) wrapped into
@@ -56,10 +87,11 @@ __device__ __forceinline__ bool project_px(const DevLevel& L, float3 x, int proj
     const float n2 = fmaf(x.x, x.x, fmaf(x.y, x.y, x.z * x.z));
     s = x.z * rsqrtf(n2);
     v = row_from_sin(L, s);
-    uc = fmaf(atan2f(x.y, x.x), L.w_over_2pi, -__ldg(L.thu + v));
+    uc = atan2_poly(x.y, x.x) * L.w_over_2pi;
+    if (L.has_theta) uc -= __ldg(L.thu + v);
   } else {
     // receiver-offset fixed point on the column angle 2 pi u_c / W
-    uc = atan2f(x.y, x.x) * L.w_over_2pi;
+    uc = atan2_poly(x.y, x.x) * L.w_over_2pi;
     s = 0.f;
     v = 0;
     for (int k = 0; k < proj_iters; ++k) {
@@ -70,7 +102,8 @@ __device__ __forceinline__ bool project_px(const DevLevel& L, float3 x, int proj
       const float n2 = fmaf(xp, xp, fmaf(yp, yp, x.z * x.z));
       s = x.z * rsqrtf(n2);
       v = row_from_sin(L, s);
-      uc = fmaf(atan2f(yp, xp), L.w_over_2pi, -__ldg(L.thu + v));
+      uc = atan2_poly(yp, xp) * L.w_over_2pi;
+      if (L.has_theta) uc -= __ldg(L.thu + v);
     }
   }
   u = wrap_col(uc, L.W);

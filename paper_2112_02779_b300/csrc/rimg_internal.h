@@ -11,12 +11,13 @@ namespace rimg {
 // from rimg_sensor and passed to kernels by value).
 struct DevLevel {
   const float4* rows;     // [H] cos phi, sin phi, cos theta_lut, sin theta_lut
-  const float2* cols;     // [W] cos, sin of 2 pi u / W
+  const float* cos_u;     // [W] cos of 2 pi u / W
+  const float* sin_u;     // [W] sin of 2 pi u / W
   const float* thu;       // [H] theta_lut * W / (2 pi)
   const int* rank2row;    // [H]
   const float* bnd;       // [H-1]
-  const int* bins;        // [n_bins]
-  int H, W, n_bins, tie_up;
+  const int4* bins;       // [n_bins] (row_lo, row_hi, boundary bits, rank at lower edge)
+  int H, W, n_bins, tie_up, bins_exact, has_theta;
   float s_lo, s_hi, bin_scale, w_over_2pi, r0, inv_w2;   // inv_w2 = 2 / W
 };
 
@@ -50,12 +51,12 @@ struct IcpLaunch {
   unsigned int* counters;   // [n_pairs]
   float huber_delta, max_corr_dist;
   int proj_iters, kahan, update;
-  int bpp, rows_per_block;
+  int bpp, rows_per_block, threads;
 };
 
 // Blocks per pair and rows per block for a level (depends on the batch and
 // the device's resident-block capacity).
-void icp_grid(int H, int W, int n_pairs, int* bpp, int* rows_per_block);
+void icp_grid(int H, int W, int n_pairs, int* bpp, int* rows_per_block, int* threads);
 cudaError_t launch_icp(const IcpLaunch& a, cudaStream_t st);
 
 constexpr int kIcpThreads = 256;
