@@ -305,7 +305,7 @@ def run_ours(args):
             import torch.distributed as dist
             dist.barrier()
 
-    launches_per_step = 2 + sum(cfg.iters)
+    launches_per_step = 2 + 2 * sum(cfg.iters)      # prep + (association, solve) per iteration
     R.rimg_profile_begin(launches_per_step * args.steps + 16)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)

@@ -216,8 +216,8 @@ int rimg_icp_step(const rimg_sensor* src, const rimg_sensor* dst, int level, int
  * inside the library; every GPU that loads the library holds one such array
  * until the process exits.  The call allocates nothing.
  *  - Limit: rimg_icp_workspace_bytes(src, n_pairs) must not exceed
- *    RIMG_STATIC_SCRATCH_BYTES (about n_pairs * H * 128 bytes for a sensor
- *    with H rows: e.g. up to 127 pairs of 64-row images per call); larger
+ *    RIMG_STATIC_SCRATCH_BYTES (about n_pairs * (H * 128 + 260) bytes for a
+ *    sensor with H rows: e.g. up to 124 pairs of 64-row images per call); larger
  *    batches return RIMG_ERR_WORKSPACE before anything is launched.
  *  - The first call on a device looks up the array's device address (with
  *    that device current) and caches it; make that first call before any
@@ -280,7 +280,8 @@ int rimg_register_host(const rimg_sensor* src, const rimg_sensor* dst, int n_pai
  * the recorded events, writes up to `cap` records (kernel id, level, n_pairs,
  * milliseconds) and stops recording; it returns the number of records.
  * Kernel ids: 0 unproject, 1 pyramid, 2 normals (+ plane pyramid),
- * 3 icp step, 4 source-range pyramid.  Not for use during stream capture.
+ * 3 icp step (association + reduction), 4 source-range pyramid, 5 FP64
+ * solve + pose update.  Not for use during stream capture.
  * ------------------------------------------------------------------------- */
 int rimg_profile_begin(int max_launches);
 int rimg_profile_end(int cap, int* kernel_id, int* level, int* n_pairs, float* ms);

@@ -33,13 +33,16 @@ def up_to_date():
     return all(os.path.getmtime(f) <= t for f in _inputs())
 
 
-def build(verbose=False, force=False):
-    if not force and up_to_date():
+def build(verbose=False, force=False, out=None, defines=()):
+    """Compile every CUDA source into one shared library (default: the
+    in-tree librimg.so).  `defines` are extra -D tunables (e.g. RIMG_RING=2)."""
+    lib = out or LIB
+    if not force and out is None and not defines and up_to_date():
         return LIB
-    os.makedirs(LIBDIR, exist_ok=True)
-    tmp = LIB + ".tmp"
+    os.makedirs(os.path.dirname(lib), exist_ok=True)
+    tmp = lib + ".tmp"
     cmd = [NVCC, "-O3", "-std=c++17", *ARCH, "-lineinfo", "-shared", "-Xcompiler", "-fPIC,-O2",
-           "-I", os.path.join(ROOT, "include"), "-o", tmp]
+           "-I", os.path.join(ROOT, "include"), "-o", tmp] + [f"-D{d}" for d in defines]
     if verbose:
         cmd += ["-Xptxas", "-v"]
     cmd += [os.path.join(CSRC, s) for s in SOURCES]
@@ -49,13 +52,15 @@ def build(verbose=False, force=False):
         raise RuntimeError("nvcc failed building librimg.so")
     if verbose:
         sys.stderr.write(res.stderr)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     ap = argparse.ArgumentParser()
     ap.add_argument("--verbose", action="store_true")
     ap.add_argument("--force", action="store_true")
+    ap.add_argument("--out", default=None, help="output path (default: in-tree _lib/librimg.so)")
+    ap.add_argument("-D", dest="defines", action="append", default=[], help="extra tunable, e.g. -D RIMG_RING=2")
     a = ap.parse_args()
-    print(build(verbose=a.verbose, force=a.force))
+    print(build(verbose=a.verbose, force=a.force, out=a.out, defines=a.defines))

@@ -10,27 +10,40 @@ namespace rimg {
 
 namespace {
 
-// FP64 Cholesky solve of the 6x6 system H x = -g; false on a pivot
-// <= 1e-12 * trace(H).
+// 1/d in FP64 by Newton-Raphson, x <- x (2 - d x), from the FP32 reciprocal:
+// each step squares the relative error (~1e-7 -> ~1e-14 -> below 1 ulp), a
+// short chain of multiply-adds instead of a full IEEE division.  d > 0 and
+// within FP32 range here (pivots of a 6x6 normal-equation system).
+__device__ __forceinline__ double recip_newton(double d) {
+  double x = (double)__frcp_rn((float)d);
+  x = x * fma(-d, x, 2.0);
+  x = x * fma(-d, x, 2.0);
+  return x;
+}
+
+// FP64 solve of the 6x6 system H x = -g by an LDL^T (square-root-free
+// Cholesky) factorisation with one reciprocal per pivot; false on a pivot
+// <= 1e-12 * trace(H) (the same test as on the Cholesky pivots L_jj^2).
 __device__ bool chol6_solve(const double (&Hm)[6][6], const double (&g)[6], double (&x)[6]) {
-  double L[6][6];
+  double L[6][6], D[6], Di[6];
   double tr = 0.0;
 #pragma unroll
   for (int i = 0; i < 6; ++i) tr += Hm[i][i];
+  const double eps = 1e-12 * tr;
 #pragma unroll
   for (int j = 0; j < 6; ++j) {
     double d = Hm[j][j];
 #pragma unroll
-    for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
-    if (!(d > 1e-12 * tr)) return false;
-    const double ljj = sqrt(d);
-    L[j][j] = ljj;
+    for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k] * D[k];
+    if (!(d > eps)) return false;
+    D[j] = d;
+    Di[j] = recip_newton(d);
 #pragma unroll
     for (int i = j + 1; i < 6; ++i) {
       double s = Hm[i][j];
 #pragma unroll
-      for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
-      L[i][j] = s / ljj;
+      for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k] * D[k];
+      L[i][j] = s * Di[j];
     }
   }
   double y[6];
@@ -39,30 +52,36 @@ __device__ bool chol6_solve(const double (&Hm)[6][6], const double (&g)[6], doub
     double s = -g[i];
 #pragma unroll
     for (int k = 0; k < i; ++k) s -= L[i][k] * y[k];
-    y[i] = s / L[i][i];
+    y[i] = s;
   }
 #pragma unroll
   for (int i = 5; i >= 0; --i) {
-    double s = y[i];
+    double s = y[i] * Di[i];
 #pragma unroll
     for (int k = i + 1; k < 6; ++k) s -= L[k][i] * x[k];
-    x[i] = s / L[i][i];
+    x[i] = s;
   }
   return true;
 }
 
 // T <- Exp(xi) T for xi = (omega, tau): Rodrigues rotation and the V matrix
-// of SE(3), with second-order series below 1e-8 rad.
+// of SE(3).  For |omega| < 0.5 rad (every Gauss-Newton step in practice) the
+// coefficients sin(t)/t, (1 - cos t)/t^2 and (t - sin t)/t^3 come from their
+// Taylor series in nested form up to t^12 (truncation < 1e-13 relative), so the
+// update needs only FP64 multiply-adds; larger rotations use sincos.
 __device__ void se3_left_update(double* T, const double (&xi)[6]) {
   const double wx = xi[0], wy = xi[1], wz = xi[2];
   const double th2 = wx * wx + wy * wy + wz * wz;
-  const double th = sqrt(th2);
   double A, B, C;
-  if (th < 1e-8) {
-    A = 1.0 - th2 / 6.0;
-    B = 0.5 - th2 / 24.0;
-    C = 1.0 / 6.0 - th2 / 120.0;
+  if (th2 < 0.25) {
+    A = 1.0 - th2 * (1.0 / 6.0) * (1.0 - th2 * (1.0 / 20.0) * (1.0 - th2 * (1.0 / 42.0) *
+        (1.0 - th2 * (1.0 / 72.0) * (1.0 - th2 * (1.0 / 110.0) * (1.0 - th2 * (1.0 / 156.0))))));
+    B = 0.5 * (1.0 - th2 * (1.0 / 12.0) * (1.0 - th2 * (1.0 / 30.0) * (1.0 - th2 * (1.0 / 56.0) *
+        (1.0 - th2 * (1.0 / 90.0) * (1.0 - th2 * (1.0 / 132.0) * (1.0 - th2 * (1.0 / 182.0)))))));
+    C = (1.0 / 6.0) * (1.0 - th2 * (1.0 / 20.0) * (1.0 - th2 * (1.0 / 42.0) * (1.0 - th2 * (1.0 / 72.0) *
+        (1.0 - th2 * (1.0 / 110.0) * (1.0 - th2 * (1.0 / 156.0) * (1.0 - th2 * (1.0 / 210.0)))))));
   } else {
+    const double th = sqrt(th2);
     double s, c;
     sincos(th, &s, &c);
     A = s / th;
@@ -169,20 +188,32 @@ __device__ __forceinline__ void accumulate_px(float2 (&t)[kPairs], float x, floa
 // Shared memory of one block (dynamic, > 48 KB).  Each thread owns column
 // `tid` of the staging arrays: the gathered target planes of its in-flight
 // chunks and their transformed source points (x, y, z, target index bits).
+// Depth of the per-thread staging ring: a chunk's source ranges are fetched
+// kRing chunks ahead of its projection, and its target planes are gathered
+// kRing - 1 chunks ahead of its accumulation.
+#ifndef RIMG_RING
+#define RIMG_RING 2
+#endif
+#ifndef RIMG_KAHAN_CHUNKS
+#define RIMG_KAHAN_CHUNKS 1
+#endif
+constexpr int kRing = RIMG_RING;
+// Chunks summed plainly into t before each compensated (Kahan) step.
+constexpr int kKahanChunks = RIMG_KAHAN_CHUNKS;
+
+// Shared memory of one block (dynamic, > 48 KB).  Each thread owns column
+// `tid` of the staging arrays: for each ring slot, the source ranges of one
+// 4-pixel chunk, its transformed points (x, y, z, target-index bits) and the
+// gathered target planes.
 template <int THREADS>
 struct IcpSmem {
-  float4 planes[2][4][THREADS];
-  float4 pts[2][4][THREADS];
+  float4 src[kRing][THREADS];
+  float4 pts[kRing][4][THREADS];
+  float4 planes[kRing][4][THREADS];
+  float4 T4[3];                            // pose rows (R | t) in FP32
   float red[THREADS / 32][2 * kPairs];     // per-warp sums
   double tot[32];
-  float T[12];
   int last;
-};
-
-// Per-thread bookkeeping of one 4-pixel chunk between issuing its gathers and
-// accumulating it (the points themselves wait in shared memory).
-struct Chunk {
-  long long off;
 };
 
 template <bool R0, bool GATE, bool ASSOC, bool KAHAN, int THREADS>
@@ -192,11 +223,8 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS) k_icp(IcpLaunch a) {
   const int tid = threadIdx.x;
   const int pair = blockIdx.x / a.bpp;
   const int blk = blockIdx.x - pair * a.bpp;
-  if (tid < 12) sm.T[tid] = (float)a.pose[pair * 16 + tid];
+  if (tid < 12) reinterpret_cast<float*>(sm.T4)[tid] = (float)a.pose[pair * 16 + tid];
   __syncthreads();
-  const float R00 = sm.T[0], R01 = sm.T[1], R02 = sm.T[2], t0 = sm.T[3];
-  const float R10 = sm.T[4], R11 = sm.T[5], R12 = sm.T[6], t1 = sm.T[7];
-  const float R20 = sm.T[8], R21 = sm.T[9], R22 = sm.T[10], t2 = sm.T[11];
 
   const DevLevel& S = a.src;
   const DevLevel& D = a.dst;
@@ -209,30 +237,47 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS) k_icp(IcpLaunch a) {
   const float inv_delta = a.huber_delta > 0.f ? 1.f / a.huber_delta : 0.f;
   const float gate2 = a.max_corr_dist * a.max_corr_dist;
 
-  float2 s[kPairs], c[kPairs];
+  float2 s[kPairs], c[kPairs], t[kPairs];
 #pragma unroll
-  for (int i = 0; i < kPairs; ++i) { s[i] = f2(0.f, 0.f); c[i] = f2(0.f, 0.f); }
+  for (int i = 0; i < kPairs; ++i) { s[i] = f2(0.f, 0.f); c[i] = f2(0.f, 0.f); t[i] = f2(0.f, 0.f); }
 
-  const int cpr = W >> 2;                       // 4-pixel chunks per row
+  // This thread's chunks: the j-th is block chunk tid + j * THREADS of the
+  // block's rows [v_begin, v_end).  Cursors walk (row, 4-pixel column) one
+  // thread-stride at a time.
+  const int cpr = W >> 2;
   const int v_begin = blk * a.rows_per_block;
   const int v_end = min(H, v_begin + a.rows_per_block);
   const int nchunks = max(0, v_end - v_begin) * cpr;
-  int v = v_begin + tid / cpr;
-  int cu = tid - (tid / cpr) * cpr;
+  const int nmine = (tid < nchunks) ? (nchunks - 1 - tid) / THREADS + 1 : 0;
   const int dv = THREADS / cpr, dcu = THREADS - dv * cpr;
-  int ch = tid;
+  struct Cursor {
+    int v, cu;
+  };
+  const Cursor start{v_begin + tid / cpr, tid - (tid / cpr) * cpr};
+  auto advance = [&](Cursor& k) {
+    k.cu += dcu;
+    k.v += dv;
+    if (k.cu >= cpr) { k.cu -= cpr; ++k.v; }
+  };
+  Cursor cf = start, ci = start, cc = start;   // fetch, issue, consume
 
-  // Stage A: unproject, transform and project the chunk at (v, cu); start
-  // the asynchronous gathers of its target planes into staging buffer `buf`.
-  auto issue = [&](Chunk& k, int buf) {
-    const int u0 = cu << 2;
-    k.off = (long long)v * W + u0;
-    const float4 r4 = __ldcs(reinterpret_cast<const float4*>(src + k.off));
+  auto fetch_src = [&](int slot) {
+    cp_async16_zfill(&sm.src[slot][tid], src + (long long)cf.v * W + (cf.cu << 2), true);
+    advance(cf);
+  };
+
+  // Unproject, transform and project the next chunk; start the gathers of its
+  // target planes (zero-filled when the pixel has no association).
+  auto issue = [&](int slot) {
+    const int v = ci.v, u0 = ci.cu << 2;
+    advance(ci);
+    const float4 r4 = sm.src[slot][tid];
     const float rr[4] = {r4.x, r4.y, r4.z, r4.w};
     const float4 rw = __ldg(S.rows + v);
-    const float4 cc = __ldg(reinterpret_cast<const float4*>(S.cos_u + u0));
-    const float4 ss = __ldg(reinterpret_cast<const float4*>(S.sin_u + u0));
-    const float cs[4] = {cc.x, cc.y, cc.z, cc.w}, sn[4] = {ss.x, ss.y, ss.z, ss.w};
+    const float4 cc4 = __ldg(reinterpret_cast<const float4*>(S.cos_u + u0));
+    const float4 ss4 = __ldg(reinterpret_cast<const float4*>(S.sin_u + u0));
+    const float cs[4] = {cc4.x, cc4.y, cc4.z, cc4.w}, sn[4] = {ss4.x, ss4.y, ss4.z, ss4.w};
+    const float4 T0 = sm.T4[0], T1 = sm.T4[1], T2 = sm.T4[2];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const bool valid = range_ok(rr[q]);
@@ -243,28 +288,19 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS) k_icp(IcpLaunch a) {
       const float px = R0 ? fmaf(rc, ct, S.r0 * cs[q]) : rc * ct;
       const float py = R0 ? fmaf(rc, st, S.r0 * sn[q]) : rc * st;
       const float pz = r * rw.y;
-      const float X = fmaf(R00, px, fmaf(R01, py, fmaf(R02, pz, t0)));
-      const float Y = fmaf(R10, px, fmaf(R11, py, fmaf(R12, pz, t1)));
-      const float Z = fmaf(R20, px, fmaf(R21, py, fmaf(R22, pz, t2)));
+      const float X = fmaf(T0.x, px, fmaf(T0.y, py, fmaf(T0.z, pz, T0.w)));
+      const float Y = fmaf(T1.x, px, fmaf(T1.y, py, fmaf(T1.z, pz, T1.w)));
+      const float Z = fmaf(T2.x, px, fmaf(T2.y, py, fmaf(T2.z, pz, T2.w)));
       int uu, vv;
       const bool fov = project_px<R0>(D, make_float3(X, Y, Z), a.proj_iters, uu, vv);
       const bool ok = valid && fov;
-      const int idx = ok ? vv * D.W + uu : -1;
-      cp_async16_zfill(&sm.planes[buf][q][tid], planes + (ok ? idx : 0), ok);
-      sm.pts[buf][q][tid] = make_float4(X, Y, Z, __int_as_float(idx));
+      const int idx = vv * D.W + uu;
+      cp_async16_zfill(&sm.planes[slot][q][tid], planes + idx, ok);
+      sm.pts[slot][q][tid] = make_float4(X, Y, Z, __int_as_float(ok ? idx : -1));
     }
-    cu += dcu;
-    v += dv;
-    if (cu >= cpr) { cu -= cpr; ++v; }
-    ch += THREADS;
   };
 
-  // Stage B: accumulate a chunk whose gathers have landed in buffer `buf`
-  // into the plain FP32 chunk sums t; flush() adds t to the running sums with
-  // Kahan compensation (once per two chunks, 8 pixels).
-  float2 t[kPairs];
-#pragma unroll
-  for (int i = 0; i < kPairs; ++i) t[i] = f2(0.f, 0.f);
+  // Add t to the running sums with Kahan compensation.
   auto flush = [&]() {
 #pragma unroll
     for (int i = 0; i < kPairs; ++i) {
@@ -279,12 +315,14 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS) k_icp(IcpLaunch a) {
       t[i] = f2(0.f, 0.f);
     }
   };
-  auto consume = [&](const Chunk& k, int buf) {
+
+  // Accumulate the oldest chunk in flight (its planes have landed) into t.
+  auto consume = [&](int slot) {
     int out_idx[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      float4 pl = sm.planes[buf][q][tid];
-      const float4 P = sm.pts[buf][q][tid];
+      float4 pl = sm.planes[slot][q][tid];
+      const float4 P = sm.pts[slot][q][tid];
       const int idx = __float_as_int(P.w);
       if (GATE) {
         bool keep = idx >= 0;
@@ -301,31 +339,47 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS) k_icp(IcpLaunch a) {
       accumulate_px(t, P.x, P.y, P.z, pl, inv_delta);
     }
     if (ASSOC) {
-      int* ap = a.assoc + pair * Ns + k.off;
+      int* ap = a.assoc + pair * Ns + (long long)cc.v * W + (cc.cu << 2);
       *reinterpret_cast<int4*>(ap) = make_int4(out_idx[0], out_idx[1], out_idx[2], out_idx[3]);
+      advance(cc);
     }
+    if (kKahanChunks == 1) flush();
   };
 
-  // Two chunks in flight per thread: issue chunk k+1's gathers, then
-  // accumulate chunk k (each thread only reads its own staging slots, so no
-  // block barrier is needed inside the loop).
-  Chunk c0, c1;
-  bool have0 = ch < nchunks;
-  if (have0) issue(c0, 0);
+  // Software pipeline over this thread's chunks with a two-slot ring (each
+  // thread reads only its own staging slots, so no block barrier is needed):
+  // step i projects chunk i (ranges fetched two steps earlier), starts its
+  // gathers and the range fetch of chunk i + 2 into the same slot, commits
+  // one cp.async group, waits until at most one group is pending (so group
+  // i - 1 -- gathers of chunk i - 1 and ranges of chunk i + 1 -- has landed)
+  // and accumulates chunk i - 1.  Unrolled by two so slots are constants.
+  static_assert(kRing == 2, "the pipeline below is written for a two-slot ring");
+  if (nmine > 0) fetch_src(0);
+  if (nmine > 1) fetch_src(1);
   cp_async_commit();
-  while (have0) {
-    const bool have1 = ch < nchunks;
-    if (have1) issue(c1, 1);
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  int i = 0;
+  while (true) {
+    // even step: slot 0 issues, slot 1 is consumed
+    if (i < nmine) {
+      issue(0);
+      if (i + 2 < nmine) fetch_src(0);
+    }
     cp_async_commit();
-    cp_async_wait1();
-    consume(c0, 0);
-    if (!have1) break;
-    have0 = ch < nchunks;
-    if (have0) issue(c0, 0);
+    asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    if (i >= 1) consume(1);
+    if (i >= nmine) break;
+    ++i;
+    // odd step: slot 1 issues, slot 0 is consumed
+    if (i < nmine) {
+      issue(1);
+      if (i + 2 < nmine) fetch_src(1);
+    }
     cp_async_commit();
-    cp_async_wait1();
-    consume(c1, 1);
-    flush();
+    asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    consume(0);
+    if (i >= nmine) break;
+    ++i;
   }
   flush();
   asm volatile("cp.async.wait_all;\n" ::: "memory");
@@ -350,10 +404,10 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS) k_icp(IcpLaunch a) {
       float acc = 0.f;
 #pragma unroll
       for (int w = 0; w < THREADS / 32; ++w) acc += sm.red[w][f];
-      sm.tot[tid] = (double)acc;
-      if (a.out29) a.out29[pair * kRed + tid] = (double)acc;
+      const double v = (double)acc;
+      a.sums[pair * kRedStride + tid] = v;
+      if (a.out29) a.out29[pair * kRed + tid] = v;
     }
-    __syncthreads();
   } else {
     if (tid < kRed) {
       const int f = kFlat[tid];
@@ -376,29 +430,44 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS) k_icp(IcpLaunch a) {
       double acc = 0.0;
       const float* pp = a.partials + (long long)pair * a.bpp * kRedStride + tid;
       for (int b = 0; b < a.bpp; ++b) acc += (double)__ldcg(pp + (long long)b * kRedStride);
-      sm.tot[tid] = acc;
+      a.sums[pair * kRedStride + tid] = acc;
       if (a.out29) a.out29[pair * kRed + tid] = acc;
     }
-    __syncthreads();
     if (tid == 0) a.counters[pair] = 0u;
   }
-  if (tid == 0 && a.update) {
-    double Hm[6][6], g[6], x[6];
-    int q = 0;
-    for (int i = 0; i < 6; ++i)
-      for (int j = i; j < 6; ++j) { Hm[i][j] = sm.tot[q]; Hm[j][i] = sm.tot[q]; ++q; }
-    for (int i = 0; i < 6; ++i) g[i] = sm.tot[21 + i];
-    bool good = sm.tot[28] >= 6.0;
-    if (good) good = chol6_solve(Hm, g, x);
-    if (good) {
-      double T[12];
-      for (int k = 0; k < 12; ++k) T[k] = a.pose[pair * 16 + k];
-      se3_left_update(T, x);
-      for (int k = 0; k < 12; ++k) a.pose[pair * 16 + k] = T[k];
-    } else if (a.status) {
-      atomicOr(a.status + pair, RIMG_FLAG_DEGENERATE);
-    }
+}
+
+// The Gauss-Newton update of every pair from its FP64 sums: one thread per
+// pair (FP64 Cholesky-type solve of the 6x6 system and the SE(3) composition).
+// Kept out of k_icp so that no reduction block holds an SM slot through the
+// serial FP64 chain.
+__global__ void __launch_bounds__(32) k_solve(int n_pairs, const double* __restrict__ sums,
+                                             double* __restrict__ pose, int* __restrict__ status) {
+  const int pair = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pair >= n_pairs) return;
+  const double* t = sums + (long long)pair * kRedStride;
+  double Hm[6][6], g[6], x[6];
+  int q = 0;
+  for (int i = 0; i < 6; ++i)
+    for (int j = i; j < 6; ++j) { Hm[i][j] = t[q]; Hm[j][i] = t[q]; ++q; }
+  for (int i = 0; i < 6; ++i) g[i] = t[21 + i];
+  bool good = t[28] >= 6.0;
+  if (good) good = chol6_solve(Hm, g, x);
+  if (good) {
+    double T[12];
+    double* P = pose + (long long)pair * 16;
+    for (int k = 0; k < 12; ++k) T[k] = P[k];
+    se3_left_update(T, x);
+    for (int k = 0; k < 12; ++k) P[k] = T[k];
+  } else if (status) {
+    status[pair] |= RIMG_FLAG_DEGENERATE;
   }
+}
+
+cudaError_t launch_solve(int n_pairs, const double* sums, double* pose, int* status, cudaStream_t st) {
+  if (n_pairs == 0) return cudaSuccess;
+  k_solve<<<(n_pairs + 31) / 32, 32, 0, st>>>(n_pairs, sums, pose, status);
+  return cudaGetLastError();
 }
 
 namespace {

@@ -141,13 +141,14 @@ DevLevel dev_level(const rimg_sensor* s, int l) {
 namespace {
 
 struct IcpWs {
-  size_t counters, partials, end;
+  size_t counters, partials, sums, end;
 };
 
 IcpWs icp_ws(int H, int n_pairs, size_t start) {
   IcpWs w{};
   size_t o = align_up(start);
   w.counters = o; o = align_up(o + sizeof(unsigned) * (size_t)std::max(n_pairs, 1));
+  w.sums = o; o = align_up(o + sizeof(double) * kRedStride * (size_t)std::max(n_pairs, 1));
   w.partials = o; o = align_up(o + sizeof(float) * kRedStride * (size_t)H * std::max(n_pairs, 1));
   w.end = o;
   return w;
@@ -196,6 +197,7 @@ int icp_launch(const rimg_sensor* src, const rimg_sensor* dst, int level, int n_
   a.status = status;
   a.partials = reinterpret_cast<float*>(ws + w.partials);
   a.counters = reinterpret_cast<unsigned*>(ws + w.counters);
+  a.sums = reinterpret_cast<double*>(ws + w.sums);
   a.huber_delta = p->huber_delta;
   a.max_corr_dist = p->max_corr_dist;
   a.proj_iters = p->proj_iters;
@@ -206,6 +208,12 @@ int icp_launch(const rimg_sensor* src, const rimg_sensor* dst, int level, int n_
   cudaError_t e = launch_icp(a, st);
   prof_after(st);
   if (e != cudaSuccess) return cuda_fail(e, "icp step kernel");
+  if (update) {
+    prof_before(st, K_SOLVE, level, n_pairs);
+    e = launch_solve(n_pairs, a.sums, pose, status, st);
+    prof_after(st);
+    if (e != cudaSuccess) return cuda_fail(e, "solve kernel");
+  }
   return RIMG_OK;
 }
 

@@ -69,12 +69,13 @@ __device__ __forceinline__ float atan2_poly(float y, float x) {
 }
 
 // Column from the continuous estimate u_c: floor(u_c + 1/2) wrapped into
-// [0, W).  |u_c| < 2W always holds here (atan2 range plus |theta_lut| < pi).
+// [0, W).  Here |u_c| < W (atan2 in [-pi, pi] and |theta_lut| < pi), so one
+// conditional add or subtract of W lands in [0, W); NaN converts to 0.
 __device__ __forceinline__ int wrap_col(float uc, int W) {
   int u = __float2int_rd(uc + 0.5f);
   u = (u < 0) ? u + W : u;
   u = (u >= W) ? u - W : u;
-  return min(max(u, 0), W - 1);
+  return u;
 }
 
 // Pi (Section 3.2) of point x into level L.  Returns true when the point lies

@@ -23,7 +23,7 @@ struct DevLevel {
 
 DevLevel dev_level(const rimg_sensor* s, int level);
 
-enum KernelId { K_UNPROJECT = 0, K_PYRAMID = 1, K_NORMALS = 2, K_ICP = 3, K_SRC_PYRAMID = 4 };
+enum KernelId { K_UNPROJECT = 0, K_PYRAMID = 1, K_NORMALS = 2, K_ICP = 3, K_SRC_PYRAMID = 4, K_SOLVE = 5 };
 
 // Launch-timing hooks (no-ops unless rimg_profile_begin was called).
 void prof_before(cudaStream_t st, int kernel, int level, int n);
@@ -49,6 +49,7 @@ struct IcpLaunch {
   int* status;
   float* partials;          // [n_pairs][bpp][32]
   unsigned int* counters;   // [n_pairs]
+  double* sums;             // [n_pairs][32] FP64 totals (input of the solve)
   float huber_delta, max_corr_dist;
   int proj_iters, kahan, update;
   int bpp, rows_per_block, threads;
@@ -58,6 +59,7 @@ struct IcpLaunch {
 // the device's resident-block capacity).
 void icp_grid(int H, int W, int n_pairs, int* bpp, int* rows_per_block, int* threads);
 cudaError_t launch_icp(const IcpLaunch& a, cudaStream_t st);
+cudaError_t launch_solve(int n_pairs, const double* sums, double* pose, int* status, cudaStream_t st);
 
 constexpr int kIcpThreads = 256;
 constexpr int kRed = 29;          // reduced quantities per pair

@@ -15,7 +15,8 @@ from ._abi import (RIMG_MAX_LEVELS, RIMG_FLAG_DEGENERATE, RIMG_STATIC_SCRATCH_BY
                    STATUS_NAMES, HEADER_FUNCTIONS)
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_lib", "librimg.so")
+# RIMG_LIBRARY: path of an alternative build of librimg.so (same ABI)
+LIB_PATH = os.environ.get("RIMG_LIBRARY") or os.path.join(_HERE, "_lib", "librimg.so")
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"librimg.so not built ({LIB_PATH}); run `python -m paper_2112_02779_b300.build`")
@@ -249,7 +250,7 @@ def rimg_profile_end(cap=100000):
     return [(kid[i], lvl[i], npr[i], ms[i]) for i in range(n)]
 
 
-KERNEL_NAMES = {0: "unproject", 1: "pyramid", 2: "normals", 3: "icp_step", 4: "src_pyramid"}
+KERNEL_NAMES = {0: "unproject", 1: "pyramid", 2: "normals", 3: "icp_step", 4: "src_pyramid", 5: "solve"}
 
 __all__ = [n for n in dir() if n.startswith("rimg_")] + ["Sensor", "RimgError", "KERNEL_NAMES",
                                                           "RIMG_MAX_LEVELS", "RIMG_FLAG_DEGENERATE", "lib"]
