@@ -83,13 +83,16 @@ typedef struct rimg_sensor {
 
 /* Method parameters.  Defaults (rimg_default_params): huber_delta 0.5 m (the
  * outdoor kernel size of Section 6.1), no distance gate, normal_rel_jump 0.1,
- * proj_iters 3, kahan 1. */
+ * proj_iters 3, kahan 1, streams 2.  `streams` does not change results: pairs
+ * are independent, and each sub-batch of at least 32 pairs runs on its own
+ * internal stream forked from and joined back into the caller's stream. */
 typedef struct rimg_params {
   float huber_delta;        /* pseudo-Huber kernel size (m); <= 0: plain least squares */
   float max_corr_dist;      /* reject pairs with |x - q| > max_corr_dist; <= 0: off */
   float normal_rel_jump;    /* a normal needs |r_nb - r_c| <= normal_rel_jump * r_c, in [0, 0.5) */
   int proj_iters;           /* receiver-offset fixed-point steps when r0 != 0 (1..16) */
   int kahan;                /* 1: Kahan-compensated FP32 accumulation of J^T W J / J^T W e */
+  int streams;              /* rimg_register: concurrent sub-batches (internal streams), 1..4 */
 } rimg_params;
 
 /* Fill *p with the defaults above.  Host only. */

@@ -26,7 +26,8 @@ class rimg_sensor(ctypes.Structure):
 
 class rimg_params(ctypes.Structure):
     _fields_ = [("huber_delta", ctypes.c_float), ("max_corr_dist", ctypes.c_float),
-                ("normal_rel_jump", ctypes.c_float), ("proj_iters", ctypes.c_int), ("kahan", ctypes.c_int)]
+                ("normal_rel_jump", ctypes.c_float), ("proj_iters", ctypes.c_int), ("kahan", ctypes.c_int),
+                ("streams", ctypes.c_int)]
 
 
 # Every function include/rimg.h declares (checked against the header and the

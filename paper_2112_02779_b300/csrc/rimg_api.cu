@@ -77,6 +77,7 @@ int check_params(const rimg_params* p) {
   if (!std::isfinite(p->huber_delta) || !std::isfinite(p->max_corr_dist)) return RIMG_ERR_INVALID_ARG;
   if (!(p->normal_rel_jump >= 0.f && p->normal_rel_jump < 0.5f)) return RIMG_ERR_INVALID_ARG;
   if (p->proj_iters < 1 || p->proj_iters > 16) return RIMG_ERR_INVALID_ARG;
+  if (p->streams < 1 || p->streams > 4) return RIMG_ERR_INVALID_ARG;
   return RIMG_OK;
 }
 
@@ -179,10 +180,24 @@ RegWs reg_ws(int H, int W, int n_pairs, int levels, size_t start) {
   return r;
 }
 
+struct IcpScratch {
+  unsigned* counters;   // [n_pairs], zero between launches
+  double* sums;         // [n_pairs][32]
+  float* partials;      // [n_pairs][H][32] (at most H blocks per pair)
+};
+
+IcpScratch icp_scratch(char* ws, const IcpWs& w, int H, int p0) {
+  IcpScratch s;
+  s.counters = reinterpret_cast<unsigned*>(ws + w.counters) + p0;
+  s.sums = reinterpret_cast<double*>(ws + w.sums) + (size_t)p0 * kRedStride;
+  s.partials = reinterpret_cast<float*>(ws + w.partials) + (size_t)p0 * H * kRedStride;
+  return s;
+}
+
 int icp_launch(const rimg_sensor* src, const rimg_sensor* dst, int level, int n_pairs,
                const float* src_range_l, const float* dst_planes_l, const float* dst_range_l,
                double* pose, const rimg_params* p, int update, double* out29, int32_t* assoc,
-               int* status, char* ws, const IcpWs& w, cudaStream_t st) {
+               int* status, const IcpScratch& w, cudaStream_t st) {
   if (p->max_corr_dist > 0.f && !dst_range_l) return RIMG_ERR_INVALID_ARG;
   IcpLaunch a{};
   a.src = dev_level(src, level);
@@ -195,9 +210,9 @@ int icp_launch(const rimg_sensor* src, const rimg_sensor* dst, int level, int n_
   a.out29 = out29;
   a.assoc = assoc;
   a.status = status;
-  a.partials = reinterpret_cast<float*>(ws + w.partials);
-  a.counters = reinterpret_cast<unsigned*>(ws + w.counters);
-  a.sums = reinterpret_cast<double*>(ws + w.sums);
+  a.partials = w.partials;
+  a.counters = w.counters;
+  a.sums = w.sums;
   a.huber_delta = p->huber_delta;
   a.max_corr_dist = p->max_corr_dist;
   a.proj_iters = p->proj_iters;
@@ -217,24 +232,33 @@ int icp_launch(const rimg_sensor* src, const rimg_sensor* dst, int level, int n_
   return RIMG_OK;
 }
 
-int register_device(const rimg_sensor* src, const rimg_sensor* dst, int n_pairs, const float* src_range,
-                    const float* dst_range, const double* T_init, double* T_out, int levels,
-                    const int* iters, const rimg_params* p, int* status, char* ws,
-                    const RegWs& R, cudaStream_t st) {
+// Registration of the pairs [p0, p0 + n) of a batch on one stream; every
+// buffer is addressed through the per-pair offsets of that range.
+int register_slice(const rimg_sensor* src, const rimg_sensor* dst, int p0, int n, const float* src_range,
+                   const float* dst_range, const double* T_init, double* T_out, int levels, const int* iters,
+                   const rimg_params* p, int* status, char* ws, const RegWs& R, cudaStream_t st) {
   const int H = src->H, W = src->W;
-  if (status) RIMG_CUDA(cudaMemsetAsync(status, 0, sizeof(int) * n_pairs, st));
+  const size_t N = (size_t)H * W;
+  src_range += p0 * N;
+  dst_range += p0 * N;
+  T_init += 16 * (size_t)p0;
+  T_out += 16 * (size_t)p0;
+  if (status) status += p0;
+  if (status) RIMG_CUDA(cudaMemsetAsync(status, 0, sizeof(int) * n, st));
   if (T_out != T_init)
-    RIMG_CUDA(cudaMemcpyAsync(T_out, T_init, sizeof(double) * 16 * n_pairs, cudaMemcpyDeviceToDevice, st));
-  RIMG_CUDA(cudaMemsetAsync(ws + R.icp.counters, 0, sizeof(unsigned) * n_pairs, st));
+    RIMG_CUDA(cudaMemcpyAsync(T_out, T_init, sizeof(double) * 16 * n, cudaMemcpyDeviceToDevice, st));
+  const IcpScratch scr = icp_scratch(ws, R.icp, H, p0);
+  RIMG_CUDA(cudaMemsetAsync(scr.counters, 0, sizeof(unsigned) * n, st));
   // Target planes of every level (normals at the finest level, strided pyramid).
   float* planes[RIMG_MAX_LEVELS] = {};
   float* srcl[RIMG_MAX_LEVELS] = {};
   float* dstl[RIMG_MAX_LEVELS] = {};
   for (int l = 0; l < levels; ++l) {
-    planes[l] = reinterpret_cast<float*>(ws + R.planes[l]);
+    const size_t Nl = (size_t)(H >> l) * (W >> l);
+    planes[l] = reinterpret_cast<float*>(ws + R.planes[l]) + 4 * Nl * p0;
     if (l >= 1) {
-      srcl[l] = reinterpret_cast<float*>(ws + R.src_lvl[l]);
-      dstl[l] = reinterpret_cast<float*>(ws + R.dst_lvl[l]);
+      srcl[l] = reinterpret_cast<float*>(ws + R.src_lvl[l]) + Nl * p0;
+      dstl[l] = reinterpret_cast<float*>(ws + R.dst_lvl[l]) + Nl * p0;
     }
   }
   const bool gate = p->max_corr_dist > 0.f;
@@ -242,18 +266,18 @@ int register_device(const rimg_sensor* src, const rimg_sensor* dst, int n_pairs,
   // levels than the sensor has, so build a view limited to `levels`.
   rimg_sensor dview = *dst;
   dview.levels = levels;
-  prof_before(st, K_NORMALS, 0, n_pairs);
-  cudaError_t e = launch_normals(&dview, n_pairs, dst_range, p->normal_rel_jump, planes, nullptr, st);
+  prof_before(st, K_NORMALS, 0, n);
+  cudaError_t e = launch_normals(&dview, n, dst_range, p->normal_rel_jump, planes, nullptr, st);
   prof_after(st);
   if (e != cudaSuccess) return cuda_fail(e, "normals kernel");
   if (levels > 1) {
-    prof_before(st, K_SRC_PYRAMID, 1, n_pairs);
-    e = launch_pyramid(n_pairs, H, W, levels, 1, src_range, srcl, st);
+    prof_before(st, K_SRC_PYRAMID, 1, n);
+    e = launch_pyramid(n, H, W, levels, 1, src_range, srcl, st);
     prof_after(st);
     if (e != cudaSuccess) return cuda_fail(e, "pyramid kernel");
     if (gate) {   // the distance gate reads the target ranges of every level
-      prof_before(st, K_PYRAMID, 1, n_pairs);
-      e = launch_pyramid(n_pairs, H, W, levels, 1, dst_range, dstl, st);
+      prof_before(st, K_PYRAMID, 1, n);
+      e = launch_pyramid(n, H, W, levels, 1, dst_range, dstl, st);
       prof_after(st);
       if (e != cudaSuccess) return cuda_fail(e, "pyramid kernel");
     }
@@ -263,10 +287,56 @@ int register_device(const rimg_sensor* src, const rimg_sensor* dst, int n_pairs,
     const float* s_l = (l == 0) ? src_range : srcl[l];
     const float* d_l = gate ? ((l == 0) ? dst_range : dstl[l]) : nullptr;
     for (int it = 0; it < iters[k]; ++it) {
-      int rc = icp_launch(src, dst, l, n_pairs, s_l, planes[l], d_l, T_out, p, 1, nullptr, nullptr,
-                          status, ws, R.icp, st);
+      int rc = icp_launch(src, dst, l, n, s_l, planes[l], d_l, T_out, p, 1, nullptr, nullptr, status, scr, st);
       if (rc) return rc;
     }
+  }
+  return RIMG_OK;
+}
+
+// Internal streams for concurrent sub-batches, created once per device.
+constexpr int kMaxSubStreams = 4;
+struct SubStreams {
+  std::mutex mu;
+  int device = -1;
+  cudaStream_t s[kMaxSubStreams] = {};
+  cudaEvent_t fork = nullptr, join[kMaxSubStreams] = {};
+} g_sub;
+
+// Pairs are independent, so a batch splits into p->streams sub-batches that
+// run concurrently on internal streams forked from (and joined back into)
+// `st`: one sub-batch's FP64 solves, launch gaps and small coarse-level
+// kernels overlap another's work.
+int register_device(const rimg_sensor* src, const rimg_sensor* dst, int n_pairs, const float* src_range,
+                    const float* dst_range, const double* T_init, double* T_out, int levels,
+                    const int* iters, const rimg_params* p, int* status, char* ws,
+                    const RegWs& R, cudaStream_t st) {
+  int S = std::min(std::max(p->streams, 1), kMaxSubStreams);
+  if (n_pairs < 32 * S) S = std::max(1, n_pairs / 32);
+  if (S <= 1) return register_slice(src, dst, 0, n_pairs, src_range, dst_range, T_init, T_out, levels, iters,
+                                    p, status, ws, R, st);
+  std::lock_guard<std::mutex> lk(g_sub.mu);
+  int dev = 0;
+  RIMG_CUDA(cudaGetDevice(&dev));
+  if (g_sub.device != dev) {
+    for (int i = 0; i < kMaxSubStreams; ++i) {
+      RIMG_CUDA(cudaStreamCreateWithFlags(&g_sub.s[i], cudaStreamNonBlocking));
+      RIMG_CUDA(cudaEventCreateWithFlags(&g_sub.join[i], cudaEventDisableTiming));
+    }
+    RIMG_CUDA(cudaEventCreateWithFlags(&g_sub.fork, cudaEventDisableTiming));
+    g_sub.device = dev;
+  }
+  RIMG_CUDA(cudaEventRecord(g_sub.fork, st));
+  int p0 = 0;
+  for (int i = 0; i < S; ++i) {
+    const int n = n_pairs / S + (i < n_pairs % S ? 1 : 0);
+    RIMG_CUDA(cudaStreamWaitEvent(g_sub.s[i], g_sub.fork, 0));
+    int rc = register_slice(src, dst, p0, n, src_range, dst_range, T_init, T_out, levels, iters, p, status, ws, R,
+                            g_sub.s[i]);
+    if (rc) return rc;
+    RIMG_CUDA(cudaEventRecord(g_sub.join[i], g_sub.s[i]));
+    RIMG_CUDA(cudaStreamWaitEvent(st, g_sub.join[i], 0));
+    p0 += n;
   }
   return RIMG_OK;
 }
@@ -310,6 +380,7 @@ int rimg_default_params(rimg_params* p) {
   p->normal_rel_jump = 0.1f;
   p->proj_iters = 3;
   p->kahan = 1;
+  p->streams = 2;
   return RIMG_OK;
 }
 
@@ -538,7 +609,7 @@ int rimg_icp_step(const rimg_sensor* src, const rimg_sensor* dst, int level, int
   char* ws = static_cast<char*>(workspace);
   RIMG_CUDA(cudaMemsetAsync(ws + w.counters, 0, sizeof(unsigned) * n_pairs, st));
   return icp_launch(src, dst, level, n_pairs, src_range_l, dst_planes_l, dst_range_l, pose, p, update,
-                    out29, assoc, status, ws, w, st);
+                    out29, assoc, status, icp_scratch(ws, w, src->H, 0), st);
 }
 
 int rimg_register_workspace_bytes(const rimg_sensor* src, const rimg_sensor* dst, int n_pairs, int levels,

@@ -44,7 +44,8 @@ int main(void) {
   printf("%zu %zu %zu\n", sizeof(rimg_level), sizeof(rimg_sensor), sizeof(rimg_params));
   printf("%zu %zu %zu %zu\n", offsetof(rimg_level, off_rows), offsetof(rimg_level, off_bins),
          offsetof(rimg_sensor, d_tables), offsetof(rimg_sensor, level));
-  printf("%zu %zu\n", offsetof(rimg_params, proj_iters), offsetof(rimg_params, kahan));
+  printf("%zu %zu %zu\n", offsetof(rimg_params, proj_iters), offsetof(rimg_params, kahan),
+         offsetof(rimg_params, streams));
   return 0;
 }
 ''')
@@ -54,13 +55,13 @@ int main(void) {
     L, S, P = _abi.rimg_level, _abi.rimg_sensor, _abi.rimg_params
     assert vals == [ctypes.sizeof(L), ctypes.sizeof(S), ctypes.sizeof(P),
                     L.off_rows.offset, L.off_bins.offset, S.d_tables.offset, S.level.offset,
-                    P.proj_iters.offset, P.kahan.offset]
+                    P.proj_iters.offset, P.kahan.offset, P.streams.offset]
 
 
 def test_default_params_and_status_strings():
     p = R.rimg_default_params()
     assert p.huber_delta == pytest.approx(0.5) and p.max_corr_dist == 0.0
-    assert p.normal_rel_jump == pytest.approx(0.1) and p.proj_iters == 3 and p.kahan == 1
+    assert p.normal_rel_jump == pytest.approx(0.1) and p.proj_iters == 3 and p.kahan == 1 and p.streams == 2
     for code in _abi.STATUS_NAMES:
         assert R.rimg_status_string(code)
     assert R.rimg_status_string(12345) == "unknown status"

@@ -401,3 +401,24 @@ def test_full_size_batch_sampled_against_oracle(R):
         To, _ = oracle_register(src[i], dst[i], s, np.eye(4), 4, cfg.iters, oracle_params(cfg))
         eR, et = O.pose_error(Tg[0, i], To)
         assert eR <= 1e-4 and et <= 1e-4
+
+
+def test_register_sub_batch_streams_agree(R):
+    """Splitting a batch over internal streams changes only the FP32 summation
+    order of each pair's reduction (the block decomposition depends on the
+    sub-batch size), not the registration."""
+    cfg = CONFIGS["pair32x512"]
+    s = cfg.sensor()
+    sens = gpu_sensor(R, s, 3)
+    n = 96
+    src, dst, _ = make_pairs(cfg, range(8))
+    src, dst = np.tile(src, (12, 1, 1)), np.tile(dst, (12, 1, 1))
+    T0 = np.tile(np.eye(4), (n, 1, 1))
+    out = {}
+    for streams in (1, 2, 3):
+        params = R.rimg_default_params(huber_delta=cfg.huber_delta, streams=streams)
+        out[streams], _ = gpu_register(R, torch, sens, src, dst, T0, 3, cfg.iters, params)
+    for streams in (2, 3):
+        for i in range(n):
+            eR, et = O.pose_error(out[streams][i], out[1][i])
+            assert eR <= 1e-6 and et <= 1e-6
