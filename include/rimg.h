@@ -261,12 +261,16 @@ int rimg_register(const rimg_sensor* src, const rimg_sensor* dst, int n_pairs,
 /* ---------------------------------------------------------------------------
  * rimg_register with HOST inputs and outputs: copies src_range/dst_range
  * ([n][H][W] float32) and T_init ([n][16] float64) from host memory (pinned
- * memory overlaps best) into the workspace, registers, copies T_out (host,
- * [n][16]) and status (host int32 [n], nullable) back, and SYNCHRONISES the
- * stream before returning.  workspace >= rimg_register_host_workspace_bytes().
- * The transfer is split into chunks of pairs on `stream` so that the copy of
- * one chunk overlaps the registration of the previous one when
- * chunk_pairs < n_pairs (chunk_pairs <= 0: one chunk).
+ * memory is needed for the copies to overlap computation) into the
+ * workspace, registers, copies T_out (host, [n][16]) and status (host int32
+ * [n], nullable) back, and SYNCHRONISES the stream before returning.
+ * workspace >= rimg_register_host_workspace_bytes() (it stages the whole
+ * batch).  The batch is uploaded in chunks of chunk_pairs pairs (<= 0: one
+ * chunk; at most 64 chunks) on an internal copy stream; each chunk is
+ * registered on one of four internal compute streams as soon as its own
+ * upload has landed, so uploads overlap registrations and registrations of
+ * successive chunks overlap each other.  All internal work starts after the
+ * work already queued on `stream` and is joined back into it.
  * ------------------------------------------------------------------------- */
 int rimg_register_host_workspace_bytes(const rimg_sensor* src, const rimg_sensor* dst,
                                        int n_pairs, int levels, int chunk_pairs, size_t* bytes);
@@ -276,18 +280,35 @@ int rimg_register_host(const rimg_sensor* src, const rimg_sensor* dst, int n_pai
                        const rimg_params* p, int* status_host, int chunk_pairs, void* workspace,
                        size_t workspace_bytes, void* stream);
 
+/* The same without the final synchronisation: all copies and kernels are
+ * queued and joined into `stream`; the caller must synchronise `stream` (or
+ * wait on an event recorded after the call) before reading T_out_host /
+ * status_host and before reusing the workspace or the host input buffers.
+ * A streaming caller alternating two workspaces and two streams overlaps the
+ * upload of batch k+1 with the registration of batch k.  The internal copy
+ * and compute streams are shared by all calls on a device, so calls are
+ * ordered with each other there. */
+int rimg_register_host_async(const rimg_sensor* src, const rimg_sensor* dst, int n_pairs,
+                             const float* src_range_host, const float* dst_range_host,
+                             const double* T_init_host, double* T_out_host, int levels, const int* iters,
+                             const rimg_params* p, int* status_host, int chunk_pairs, void* workspace,
+                             size_t workspace_bytes, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Launch timing (tracing).  rimg_profile_begin(max) makes subsequent library
  * launches on any stream record a CUDA event pair around each kernel (at most
  * `max` launches; later ones are not recorded).  rimg_profile_end waits for
  * the recorded events, writes up to `cap` records (kernel id, level, n_pairs,
- * milliseconds) and stops recording; it returns the number of records.
+ * start in ms after the first record's start, duration in ms; any output
+ * pointer may be NULL) and stops recording; it returns the number of records.
+ * Launches on concurrent streams overlap in time: the start offsets let a
+ * caller take the union of intervals.
  * Kernel ids: 0 unproject, 1 pyramid, 2 normals (+ plane pyramid),
  * 3 icp step (association + reduction), 4 source-range pyramid, 5 FP64
  * solve + pose update.  Not for use during stream capture.
  * ------------------------------------------------------------------------- */
 int rimg_profile_begin(int max_launches);
-int rimg_profile_end(int cap, int* kernel_id, int* level, int* n_pairs, float* ms);
+int rimg_profile_end(int cap, int* kernel_id, int* level, int* n_pairs, float* start_ms, float* ms);
 
 #ifdef __cplusplus
 }

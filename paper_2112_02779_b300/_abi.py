@@ -37,5 +37,6 @@ HEADER_FUNCTIONS = [
     "rimg_sensor_table_bytes", "rimg_sensor_build", "rimg_unproject", "rimg_pyramid", "rimg_normals",
     "rimg_icp_workspace_bytes", "rimg_icp_step", "rimg_icp_step_static",
     "rimg_register_workspace_bytes", "rimg_register",
-    "rimg_register_host_workspace_bytes", "rimg_register_host", "rimg_profile_begin", "rimg_profile_end",
+    "rimg_register_host_workspace_bytes", "rimg_register_host", "rimg_register_host_async",
+    "rimg_profile_begin", "rimg_profile_end",
 ]

@@ -59,9 +59,10 @@ __global__ void __launch_bounds__(256) k_pyramid(int n, int H, int W, int levels
     const int v1 = pix / W1, u1 = pix - v1 * W1;
     const T val = in[img * (long long)H * W + (long long)(2 * v1) * W + 2 * u1];
     out.p[1][i] = val;
-    for (int l = 2; l < levels; ++l) {
+#pragma unroll
+    for (int l = 2; l < RIMG_MAX_LEVELS; ++l) {
       const int m = (1 << (l - 1)) - 1;
-      if ((u1 & m) | (v1 & m)) break;
+      if (l >= levels || ((u1 & m) | (v1 & m))) break;
       const int Hl = H >> l, Wl = W >> l;
       out.p[l][img * (long long)Hl * Wl + (long long)(v1 >> (l - 1)) * Wl + (u1 >> (l - 1))] = val;
     }
@@ -160,9 +161,11 @@ __global__ void __launch_bounds__(NT_X* NT_Y) k_normals(DevLevel L, int levels, 
   const long long N = (long long)H * W;
   out.p[0][img * N + (long long)v * W + u] = plane;
   if (mask0) mask0[img * N + (long long)v * W + u] = ok ? 1 : 0;
-  for (int l = 1; l < levels; ++l) {
+  // unrolled so the level pointers are read with constant indices (no local copy)
+#pragma unroll
+  for (int l = 1; l < RIMG_MAX_LEVELS; ++l) {
     const int m = (1 << l) - 1;
-    if ((u & m) | (v & m)) break;
+    if (l >= levels || ((u & m) | (v & m))) break;
     const int Hl = H >> l, Wl = W >> l;
     out.p[l][img * (long long)Hl * Wl + (long long)(v >> l) * Wl + (u >> l)] = plane;
   }

@@ -356,16 +356,36 @@ int check_register_args(const rimg_sensor* src, const rimg_sensor* dst, int n_pa
   return RIMG_OK;
 }
 
-// Host-buffer variant: a copy stream and events, created once per process.
+// Host-buffer variant: a copy stream, a pool of compute streams and events,
+// created once per device.
+constexpr int kHostStreams = 4;
+constexpr int kHostEvents = 64;
 struct HostPipe {
   std::mutex mu;
-  bool ready = false;
   int device = -1;
   cudaStream_t copy = nullptr;
-  cudaEvent_t loaded[2] = {nullptr, nullptr};
-  cudaEvent_t freed[2] = {nullptr, nullptr};
+  cudaStream_t comp[kHostStreams] = {};
+  cudaEvent_t start = nullptr;
+  cudaEvent_t loaded[kHostEvents] = {};
+  cudaEvent_t done[kHostStreams] = {};
 } g_pipe;
 
+struct HostWs {
+  size_t src, dst, T, S;
+  RegWs reg;
+};
+
+HostWs host_ws(int H, int W, int n_pairs, int levels) {
+  HostWs h{};
+  const size_t N = (size_t)H * W, n = (size_t)std::max(n_pairs, 1);
+  size_t o = 0;
+  h.src = o; o = align_up(o + sizeof(float) * N * n);
+  h.dst = o; o = align_up(o + sizeof(float) * N * n);
+  h.T = o; o = align_up(o + sizeof(double) * 16 * n);
+  h.S = o; o = align_up(o + sizeof(int) * n);
+  h.reg = reg_ws(H, W, n_pairs, levels, o);
+  return h;
+}
 }  // namespace
 }  // namespace rimg
 
@@ -647,13 +667,76 @@ int rimg_register_host_workspace_bytes(const rimg_sensor* src, const rimg_sensor
   if ((rc = check_sensor(dst))) return rc;
   if (src->H != dst->H || src->W != dst->W) return RIMG_ERR_MISMATCH;
   if (n_pairs < 0 || levels < 1 || levels > src->levels || levels > dst->levels) return RIMG_ERR_INVALID_ARG;
-  const int chunk = (chunk_pairs <= 0 || chunk_pairs > n_pairs) ? std::max(n_pairs, 1) : chunk_pairs;
+  (void)chunk_pairs;
+  *bytes = host_ws(src->H, src->W, n_pairs, levels).reg.end;
+  return RIMG_OK;
+}
+
+int rimg_register_host_async(const rimg_sensor* src, const rimg_sensor* dst, int n_pairs,
+                             const float* src_range_host, const float* dst_range_host, const double* T_init_host,
+                             double* T_out_host, int levels, const int* iters, const rimg_params* p,
+                             int* status_host, int chunk_pairs, void* workspace, size_t workspace_bytes,
+                             void* stream) {
+  int rc = check_register_args(src, dst, n_pairs, levels, iters, p);
+  if (rc) return rc;
+  if (n_pairs == 0) return RIMG_OK;
+  if (!src_range_host || !dst_range_host || !T_init_host || !T_out_host || !workspace) return RIMG_ERR_INVALID_ARG;
+  const HostWs hw = host_ws(src->H, src->W, n_pairs, levels);
+  if (!aligned(workspace) || workspace_bytes < hw.reg.end) return RIMG_ERR_WORKSPACE;
+  int chunk = (chunk_pairs <= 0 || chunk_pairs > n_pairs) ? n_pairs : chunk_pairs;
+  if ((n_pairs + chunk - 1) / chunk > kHostEvents) chunk = (n_pairs + kHostEvents - 1) / kHostEvents;
   const size_t N = (size_t)src->H * src->W;
-  size_t o = 0;
-  for (int b = 0; b < 2; ++b) o = align_up(o + sizeof(float) * N * chunk * 2);   // src + dst per buffer
-  o = align_up(o + sizeof(double) * 16 * std::max(n_pairs, 1));
-  o = align_up(o + sizeof(int) * std::max(n_pairs, 1));
-  *bytes = reg_ws(src->H, src->W, chunk, levels, o).end;
+  char* ws = static_cast<char*>(workspace);
+  float* d_src = reinterpret_cast<float*>(ws + hw.src);
+  float* d_dst = reinterpret_cast<float*>(ws + hw.dst);
+  double* dT = reinterpret_cast<double*>(ws + hw.T);
+  int* dS = reinterpret_cast<int*>(ws + hw.S);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+
+  std::lock_guard<std::mutex> lk(g_pipe.mu);
+  int dev = 0;
+  RIMG_CUDA(cudaGetDevice(&dev));
+  if (g_pipe.device != dev) {
+    RIMG_CUDA(cudaStreamCreateWithFlags(&g_pipe.copy, cudaStreamNonBlocking));
+    for (int i = 0; i < kHostStreams; ++i) {
+      RIMG_CUDA(cudaStreamCreateWithFlags(&g_pipe.comp[i], cudaStreamNonBlocking));
+      RIMG_CUDA(cudaEventCreateWithFlags(&g_pipe.done[i], cudaEventDisableTiming));
+    }
+    for (int i = 0; i < kHostEvents; ++i)
+      RIMG_CUDA(cudaEventCreateWithFlags(&g_pipe.loaded[i], cudaEventDisableTiming));
+    RIMG_CUDA(cudaEventCreateWithFlags(&g_pipe.start, cudaEventDisableTiming));
+    g_pipe.device = dev;
+  }
+  // Everything starts after the work already queued on `stream`.  The copy
+  // stream uploads chunk after chunk; chunk k's registration runs on compute
+  // stream k % 4 as soon as its own inputs have landed, so uploads overlap
+  // registrations and registrations of successive chunks overlap each other.
+  // Every chunk uses its own slice of the staging buffers and the workspace.
+  RIMG_CUDA(cudaEventRecord(g_pipe.start, st));
+  RIMG_CUDA(cudaStreamWaitEvent(g_pipe.copy, g_pipe.start, 0));
+  for (int i = 0; i < kHostStreams; ++i) RIMG_CUDA(cudaStreamWaitEvent(g_pipe.comp[i], g_pipe.start, 0));
+  RIMG_CUDA(cudaMemcpyAsync(dT, T_init_host, sizeof(double) * 16 * n_pairs, cudaMemcpyHostToDevice, g_pipe.copy));
+  int k = 0;
+  for (int off = 0; off < n_pairs; off += chunk, ++k) {
+    const int cnt = std::min(chunk, n_pairs - off);
+    RIMG_CUDA(cudaMemcpyAsync(d_src + N * off, src_range_host + N * off, sizeof(float) * N * cnt,
+                              cudaMemcpyHostToDevice, g_pipe.copy));
+    RIMG_CUDA(cudaMemcpyAsync(d_dst + N * off, dst_range_host + N * off, sizeof(float) * N * cnt,
+                              cudaMemcpyHostToDevice, g_pipe.copy));
+    RIMG_CUDA(cudaEventRecord(g_pipe.loaded[k], g_pipe.copy));
+    cudaStream_t cs = g_pipe.comp[k % kHostStreams];
+    RIMG_CUDA(cudaStreamWaitEvent(cs, g_pipe.loaded[k], 0));
+    rc = register_slice(src, dst, off, cnt, d_src, d_dst, dT, dT, levels, iters, p, dS, ws, hw.reg, cs);
+    if (rc) return rc;
+    RIMG_CUDA(cudaMemcpyAsync(T_out_host + 16 * off, dT + 16 * off, sizeof(double) * 16 * cnt,
+                              cudaMemcpyDeviceToHost, cs));
+    if (status_host)
+      RIMG_CUDA(cudaMemcpyAsync(status_host + off, dS + off, sizeof(int) * cnt, cudaMemcpyDeviceToHost, cs));
+  }
+  for (int i = 0; i < kHostStreams; ++i) {
+    RIMG_CUDA(cudaEventRecord(g_pipe.done[i], g_pipe.comp[i]));
+    RIMG_CUDA(cudaStreamWaitEvent(st, g_pipe.done[i], 0));
+  }
   return RIMG_OK;
 }
 
@@ -661,68 +744,10 @@ int rimg_register_host(const rimg_sensor* src, const rimg_sensor* dst, int n_pai
                        const float* dst_range_host, const double* T_init_host, double* T_out_host, int levels,
                        const int* iters, const rimg_params* p, int* status_host, int chunk_pairs, void* workspace,
                        size_t workspace_bytes, void* stream) {
-  int rc = check_register_args(src, dst, n_pairs, levels, iters, p);
+  int rc = rimg_register_host_async(src, dst, n_pairs, src_range_host, dst_range_host, T_init_host, T_out_host,
+                                    levels, iters, p, status_host, chunk_pairs, workspace, workspace_bytes, stream);
   if (rc) return rc;
-  if (n_pairs == 0) return RIMG_OK;
-  if (!src_range_host || !dst_range_host || !T_init_host || !T_out_host || !workspace) return RIMG_ERR_INVALID_ARG;
-  size_t need = 0;
-  rimg_register_host_workspace_bytes(src, dst, n_pairs, levels, chunk_pairs, &need);
-  if (!aligned(workspace) || workspace_bytes < need) return RIMG_ERR_WORKSPACE;
-  const int chunk = (chunk_pairs <= 0 || chunk_pairs > n_pairs) ? n_pairs : chunk_pairs;
-  const size_t N = (size_t)src->H * src->W;
-  char* ws = static_cast<char*>(workspace);
-  size_t o = 0;
-  float* buf[2];
-  for (int b = 0; b < 2; ++b) {
-    buf[b] = reinterpret_cast<float*>(ws + o);
-    o = align_up(o + sizeof(float) * N * chunk * 2);
-  }
-  double* dT = reinterpret_cast<double*>(ws + o);
-  o = align_up(o + sizeof(double) * 16 * n_pairs);
-  int* dS = reinterpret_cast<int*>(ws + o);
-  o = align_up(o + sizeof(int) * n_pairs);
-  const RegWs R = reg_ws(src->H, src->W, chunk, levels, o);
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-
-  std::lock_guard<std::mutex> lk(g_pipe.mu);
-  int dev = 0;
-  RIMG_CUDA(cudaGetDevice(&dev));
-  if (!g_pipe.ready || g_pipe.device != dev) {
-    RIMG_CUDA(cudaStreamCreateWithFlags(&g_pipe.copy, cudaStreamNonBlocking));
-    for (int b = 0; b < 2; ++b) {
-      RIMG_CUDA(cudaEventCreateWithFlags(&g_pipe.loaded[b], cudaEventDisableTiming));
-      RIMG_CUDA(cudaEventCreateWithFlags(&g_pipe.freed[b], cudaEventDisableTiming));
-    }
-    g_pipe.ready = true;
-    g_pipe.device = dev;
-  }
-  // the copy stream must not run ahead of work already queued on `stream`
-  RIMG_CUDA(cudaEventRecord(g_pipe.freed[0], st));
-  RIMG_CUDA(cudaEventRecord(g_pipe.freed[1], st));
-  RIMG_CUDA(cudaMemcpyAsync(dT, T_init_host, sizeof(double) * 16 * n_pairs, cudaMemcpyHostToDevice, st));
-  int k = 0;
-  for (int off = 0; off < n_pairs; off += chunk, ++k) {
-    const int b = k & 1;
-    const int cnt = std::min(chunk, n_pairs - off);
-    float* d_src = buf[b];
-    float* d_dst = buf[b] + N * chunk;
-    RIMG_CUDA(cudaStreamWaitEvent(g_pipe.copy, g_pipe.freed[b], 0));
-    RIMG_CUDA(cudaMemcpyAsync(d_src, src_range_host + N * off, sizeof(float) * N * cnt, cudaMemcpyHostToDevice,
-                              g_pipe.copy));
-    RIMG_CUDA(cudaMemcpyAsync(d_dst, dst_range_host + N * off, sizeof(float) * N * cnt, cudaMemcpyHostToDevice,
-                              g_pipe.copy));
-    RIMG_CUDA(cudaEventRecord(g_pipe.loaded[b], g_pipe.copy));
-    RIMG_CUDA(cudaStreamWaitEvent(st, g_pipe.loaded[b], 0));
-    rc = register_device(src, dst, cnt, d_src, d_dst, dT + 16 * off, dT + 16 * off, levels, iters, p, dS + off,
-                         ws, R, st);
-    if (rc) return rc;
-    RIMG_CUDA(cudaEventRecord(g_pipe.freed[b], st));
-    RIMG_CUDA(cudaMemcpyAsync(T_out_host + 16 * off, dT + 16 * off, sizeof(double) * 16 * cnt,
-                              cudaMemcpyDeviceToHost, st));
-    if (status_host)
-      RIMG_CUDA(cudaMemcpyAsync(status_host + off, dS + off, sizeof(int) * cnt, cudaMemcpyDeviceToHost, st));
-  }
-  RIMG_CUDA(cudaStreamSynchronize(st));
+  RIMG_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
   return RIMG_OK;
 }
 
@@ -747,17 +772,19 @@ int rimg_profile_begin(int max_launches) {
   return RIMG_OK;
 }
 
-int rimg_profile_end(int cap, int* kernel_id, int* level, int* n_pairs, float* ms) {
+int rimg_profile_end(int cap, int* kernel_id, int* level, int* n_pairs, float* start_ms, float* ms) {
   std::lock_guard<std::mutex> lk(g_prof.mu);
   g_prof.on = false;
   const int n = std::min(cap, g_prof.n);
   for (int i = 0; i < n; ++i) {
     RIMG_CUDA(cudaEventSynchronize(g_prof.ev1[i]));
-    float t = 0.f;
+    float t = 0.f, t0 = 0.f;
     RIMG_CUDA(cudaEventElapsedTime(&t, g_prof.ev0[i], g_prof.ev1[i]));
+    RIMG_CUDA(cudaEventElapsedTime(&t0, g_prof.ev0[0], g_prof.ev0[i]));
     if (kernel_id) kernel_id[i] = g_prof.kid[i];
     if (level) level[i] = g_prof.lvl[i];
     if (n_pairs) n_pairs[i] = g_prof.np[i];
+    if (start_ms) start_ms[i] = t0;
     if (ms) ms[i] = t;
   }
   g_prof.n = 0;

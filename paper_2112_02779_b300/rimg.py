@@ -55,8 +55,10 @@ _sig("rimg_register_host_workspace_bytes", _c_int, _P(rimg_sensor), _P(rimg_sens
      _c_int, _P(_c_size))
 _sig("rimg_register_host", _c_int, _P(rimg_sensor), _P(rimg_sensor), _c_int, _vp, _vp, _vp, _vp, _c_int,
      _P(_c_int), _P(rimg_params), _vp, _c_int, _vp, _c_size, _vp)
+_sig("rimg_register_host_async", _c_int, _P(rimg_sensor), _P(rimg_sensor), _c_int, _vp, _vp, _vp, _vp, _c_int,
+     _P(_c_int), _P(rimg_params), _vp, _c_int, _vp, _c_size, _vp)
 _sig("rimg_profile_begin", _c_int, _c_int)
-_sig("rimg_profile_end", _c_int, _c_int, _P(_c_int), _P(_c_int), _P(_c_int), _P(ctypes.c_float))
+_sig("rimg_profile_end", _c_int, _c_int, _P(_c_int), _P(_c_int), _P(_c_int), _P(ctypes.c_float), _P(ctypes.c_float))
 
 
 class RimgError(RuntimeError):
@@ -234,20 +236,31 @@ def rimg_register_host(src, dst, n_pairs, src_range_host, dst_range_host, T_init
         _ptr(workspace), workspace.numel() if workspace is not None else 0, _stream(stream)))
 
 
+def rimg_register_host_async(src, dst, n_pairs, src_range_host, dst_range_host, T_init_host, T_out_host, levels,
+                             iters, params, status_host=None, chunk_pairs=0, workspace=None, stream=None):
+    """Queue the host-buffer registration without synchronising; the caller
+    synchronises `stream` before reading outputs or reusing any buffer."""
+    _check("rimg_register_host_async", _lib.rimg_register_host_async(
+        src.ref(), dst.ref(), n_pairs, _ptr(src_range_host), _ptr(dst_range_host), _ptr(T_init_host),
+        _ptr(T_out_host), levels, _iters(iters), ctypes.byref(params), _ptr(status_host), int(chunk_pairs),
+        _ptr(workspace), workspace.numel() if workspace is not None else 0, _stream(stream)))
+
+
 def rimg_profile_begin(max_launches):
     _check("rimg_profile_begin", _lib.rimg_profile_begin(max_launches))
 
 
 def rimg_profile_end(cap=100000):
-    """Returns a list of (kernel_id, level, n_pairs, ms) records."""
+    """Returns a list of (kernel_id, level, n_pairs, start_ms, ms) records."""
     kid = (_c_int * cap)()
     lvl = (_c_int * cap)()
     npr = (_c_int * cap)()
+    t0 = (ctypes.c_float * cap)()
     ms = (ctypes.c_float * cap)()
-    n = _lib.rimg_profile_end(cap, kid, lvl, npr, ms)
+    n = _lib.rimg_profile_end(cap, kid, lvl, npr, t0, ms)
     if n < 0:
         raise RimgError("rimg_profile_end", n)
-    return [(kid[i], lvl[i], npr[i], ms[i]) for i in range(n)]
+    return [(kid[i], lvl[i], npr[i], t0[i], ms[i]) for i in range(n)]
 
 
 KERNEL_NAMES = {0: "unproject", 1: "pyramid", 2: "normals", 3: "icp_step", 4: "src_pyramid", 5: "solve"}

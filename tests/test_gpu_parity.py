@@ -422,3 +422,40 @@ def test_register_sub_batch_streams_agree(R):
         for i in range(n):
             eR, et = O.pose_error(out[streams][i], out[1][i])
             assert eR <= 1e-6 and et <= 1e-6
+
+
+def test_register_host_async_two_streams(R):
+    """Two asynchronous host-buffer registrations queued back to back on two
+    streams with separate workspaces give the same poses as the synchronous
+    call (the second batch is the first one reversed)."""
+    cfg = CONFIGS["pair32x512"]
+    s = cfg.sensor()
+    sens = gpu_sensor(R, s, 3)
+    params = R.rimg_default_params(huber_delta=cfg.huber_delta)
+    n = 40
+    src, dst, _ = make_pairs(cfg, range(8))
+    src, dst = np.tile(src, (5, 1, 1)), np.tile(dst, (5, 1, 1))
+    batches = [(src, dst), (np.ascontiguousarray(src[::-1]), np.ascontiguousarray(dst[::-1]))]
+    T0 = torch.from_numpy(np.tile(np.eye(4), (n, 1, 1)).reshape(n, 16).copy()).pin_memory()
+    nbytes = R.rimg_register_host_workspace_bytes(sens, sens, n, 3, 16)
+    ref, outs, keep = [], [], []
+    for bs, bd in batches:
+        hs, hd = torch.from_numpy(bs).pin_memory(), torch.from_numpy(bd).pin_memory()
+        out = torch.zeros((n, 16), dtype=torch.float64).pin_memory()
+        ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        R.rimg_register_host(sens, sens, n, hs, hd, T0, out, 3, cfg.iters, params, None, 16, ws)
+        ref.append(out.numpy().copy())
+        keep.append((hs, hd, ws))
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    # each queued call needs its own workspace, alive until its stream is drained
+    wss = [torch.empty(nbytes, dtype=torch.uint8, device="cuda") for _ in range(2)]
+    for j, (hs, hd, _) in enumerate(keep):
+        out = torch.full((n, 16), np.nan, dtype=torch.float64).pin_memory()
+        R.rimg_register_host_async(sens, sens, n, hs, hd, T0, out, 3, cfg.iters, params, None, 16, wss[j],
+                                   streams[j])
+        outs.append(out)
+    for st in streams:
+        st.synchronize()
+    for j in range(2):
+        assert np.array_equal(outs[j].numpy(), ref[j])
+    assert np.allclose(ref[0], ref[1][::-1], atol=1e-9)
