@@ -259,6 +259,48 @@ int rimg_register(const rimg_sensor* src, const rimg_sensor* dst, int n_pairs,
                   void* workspace, size_t workspace_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Uneven batches: several groups, each a batch of pairs of one sensor pair
+ * (one image size) with its own schedule and parameters, registered in one
+ * call.  Every group splits into params->streams sub-batches of >= 32 pairs;
+ * all sub-batches of all groups are spread over eight internal streams
+ * (largest first, to the least-loaded stream) forked from and joined back
+ * into `stream`, so the groups run concurrently.  The call queues work only
+ * (no synchronisation, no allocation) and can be captured in a CUDA graph
+ * once the library has been used on the device (the first call creates the
+ * internal streams and events).  Semantics per group are those of
+ * rimg_register.  workspace: device, 256-byte aligned, >=
+ * rimg_register_groups_workspace_bytes().
+ * ------------------------------------------------------------------------- */
+typedef struct rimg_group {
+  const rimg_sensor* src;
+  const rimg_sensor* dst;
+  int n_pairs;
+  int levels;
+  const int* iters;           /* HOST, coarse -> fine, `levels` entries */
+  const rimg_params* params;
+  const float* src_range;     /* device [n_pairs][H][W] */
+  const float* dst_range;     /* device [n_pairs][H][W] */
+  const double* T_init;       /* device [n_pairs][16] */
+  double* T_out;              /* device [n_pairs][16] (may alias T_init) */
+  int* status;                /* device [n_pairs], nullable */
+} rimg_group;
+
+int rimg_register_groups_workspace_bytes(int n_groups, const rimg_group* groups, size_t* bytes);
+int rimg_register_groups(int n_groups, const rimg_group* groups, void* workspace, size_t workspace_bytes,
+                         void* stream);
+
+/* Autotuner for the association kernel's launch shape (threads per block and
+ * blocks per pair, i.e. rows per block) at every level of every group, for
+ * the sub-batch sizes rimg_register_groups will use.  It builds each group's
+ * pyramids in the workspace, times every candidate shape on the group's own
+ * data (without updating poses; T_out receives a copy of T_init) and keeps
+ * the fastest in a process-wide table that later launches of the same
+ * (level size, pairs) use.  SYNCHRONOUS; returns the number of entries set
+ * (>= 0) or a negative status.  rimg_autotune_clear empties the table. */
+int rimg_autotune(int n_groups, const rimg_group* groups, void* workspace, size_t workspace_bytes, void* stream);
+int rimg_autotune_clear(void);
+
+/* ---------------------------------------------------------------------------
  * rimg_register with HOST inputs and outputs: copies src_range/dst_range
  * ([n][H][W] float32) and T_init ([n][16] float64) from host memory (pinned
  * memory is needed for the copies to overlap computation) into the

@@ -30,6 +30,14 @@ class rimg_params(ctypes.Structure):
                 ("streams", ctypes.c_int)]
 
 
+class rimg_group(ctypes.Structure):
+    _fields_ = [("src", ctypes.POINTER(rimg_sensor)), ("dst", ctypes.POINTER(rimg_sensor)),
+                ("n_pairs", ctypes.c_int), ("levels", ctypes.c_int), ("iters", ctypes.POINTER(ctypes.c_int)),
+                ("params", ctypes.POINTER(rimg_params)), ("src_range", ctypes.c_void_p),
+                ("dst_range", ctypes.c_void_p), ("T_init", ctypes.c_void_p), ("T_out", ctypes.c_void_p),
+                ("status", ctypes.c_void_p)]
+
+
 # Every function include/rimg.h declares (checked against the header and the
 # library's exports by the CPU test-suite).
 HEADER_FUNCTIONS = [
@@ -37,6 +45,7 @@ HEADER_FUNCTIONS = [
     "rimg_sensor_table_bytes", "rimg_sensor_build", "rimg_unproject", "rimg_pyramid", "rimg_normals",
     "rimg_icp_workspace_bytes", "rimg_icp_step", "rimg_icp_step_static",
     "rimg_register_workspace_bytes", "rimg_register",
+    "rimg_register_groups_workspace_bytes", "rimg_register_groups", "rimg_autotune", "rimg_autotune_clear",
     "rimg_register_host_workspace_bytes", "rimg_register_host", "rimg_register_host_async",
     "rimg_profile_begin", "rimg_profile_end",
 ]

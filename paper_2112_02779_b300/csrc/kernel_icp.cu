@@ -4,6 +4,11 @@
 // shuffle, block and one-pass grid reduction (last-block-done counter, no
 // spinning); the last block of each pair reduces in FP64, solves the 6x6
 // system by Cholesky and composes the SE(3) update.
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <utility>
+
 #include "rimg_device.cuh"
 
 namespace rimg {
@@ -485,7 +490,40 @@ int occupancy() {
 }
 }  // namespace
 
+namespace {
+// Launch shapes chosen by rimg_autotune, keyed by (level rows, columns, pairs).
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, std::pair<int, int>> g_tune;
+}  // namespace
+
+void icp_tune_set(int H, int W, int n_pairs, int threads, int bpp) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[std::make_tuple(H, W, n_pairs)] = std::make_pair(threads, bpp);
+}
+
+void icp_tune_clear() {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune.clear();
+}
+
+int icp_tune_size() {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  return (int)g_tune.size();
+}
+
 void icp_grid(int H, int W, int n_pairs, int* bpp, int* rows_per_block, int* threads) {
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(std::make_tuple(H, W, n_pairs));
+    if (it != g_tune.end()) {
+      const int b = std::min(std::max(it->second.second, 1), H);
+      const int rpb = (H + b - 1) / b;
+      *rows_per_block = rpb;
+      *bpp = (H + rpb - 1) / rpb;
+      *threads = it->second.first;
+      return;
+    }
+  }
   if (g_num_sms == 0) {
     int dev = 0;
     cudaGetDevice(&dev);

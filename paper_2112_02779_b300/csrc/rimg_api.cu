@@ -197,7 +197,7 @@ IcpScratch icp_scratch(char* ws, const IcpWs& w, int H, int p0) {
 int icp_launch(const rimg_sensor* src, const rimg_sensor* dst, int level, int n_pairs,
                const float* src_range_l, const float* dst_planes_l, const float* dst_range_l,
                double* pose, const rimg_params* p, int update, double* out29, int32_t* assoc,
-               int* status, const IcpScratch& w, cudaStream_t st) {
+               int* status, const IcpScratch& w, cudaStream_t st, int force_threads = 0, int force_bpp = 0) {
   if (p->max_corr_dist > 0.f && !dst_range_l) return RIMG_ERR_INVALID_ARG;
   IcpLaunch a{};
   a.src = dev_level(src, level);
@@ -219,6 +219,12 @@ int icp_launch(const rimg_sensor* src, const rimg_sensor* dst, int level, int n_
   a.kahan = p->kahan;
   a.update = update;
   icp_grid(a.src.H, a.src.W, n_pairs, &a.bpp, &a.rows_per_block, &a.threads);
+  if (force_threads > 0) {   // the autotuner's candidates
+    const int b = std::min(std::max(force_bpp, 1), a.src.H);
+    a.rows_per_block = (a.src.H + b - 1) / b;
+    a.bpp = (a.src.H + a.rows_per_block - 1) / a.rows_per_block;
+    a.threads = force_threads;
+  }
   prof_before(st, K_ICP, level, n_pairs);
   cudaError_t e = launch_icp(a, st);
   prof_after(st);
@@ -228,6 +234,58 @@ int icp_launch(const rimg_sensor* src, const rimg_sensor* dst, int level, int n_
     e = launch_solve(n_pairs, a.sums, pose, status, st);
     prof_after(st);
     if (e != cudaSuccess) return cuda_fail(e, "solve kernel");
+  }
+  return RIMG_OK;
+}
+
+// Per-level buffers of the pairs [p0, p0 + n) of a registration workspace.
+struct SliceBufs {
+  float* planes[RIMG_MAX_LEVELS];
+  float* srcl[RIMG_MAX_LEVELS];
+  float* dstl[RIMG_MAX_LEVELS];
+};
+
+SliceBufs slice_bufs(char* ws, const RegWs& R, int H, int W, int levels, int p0) {
+  SliceBufs b{};
+  for (int l = 0; l < levels; ++l) {
+    const size_t Nl = (size_t)(H >> l) * (W >> l);
+    b.planes[l] = reinterpret_cast<float*>(ws + R.planes[l]) + 4 * Nl * p0;
+    if (l >= 1) {
+      b.srcl[l] = reinterpret_cast<float*>(ws + R.src_lvl[l]) + Nl * p0;
+      b.dstl[l] = reinterpret_cast<float*>(ws + R.dst_lvl[l]) + Nl * p0;
+    }
+  }
+  return b;
+}
+
+// Normals + target plane pyramid and source (and, for the gate, target)
+// range pyramids of n pairs whose ranges start at src_range / dst_range.
+int prep_slice(const rimg_sensor* src, const rimg_sensor* dst, int n, const float* src_range, const float* dst_range,
+               int levels, const rimg_params* p, const SliceBufs& b, cudaStream_t st) {
+  const int H = src->H, W = src->W;
+  float* planes[RIMG_MAX_LEVELS];
+  float* srcl[RIMG_MAX_LEVELS];
+  float* dstl[RIMG_MAX_LEVELS];
+  for (int l = 0; l < RIMG_MAX_LEVELS; ++l) { planes[l] = b.planes[l]; srcl[l] = b.srcl[l]; dstl[l] = b.dstl[l]; }
+  // rimg_normals writes every level of dst's table set; register may use fewer
+  // levels than the sensor has, so build a view limited to `levels`.
+  rimg_sensor dview = *dst;
+  dview.levels = levels;
+  prof_before(st, K_NORMALS, 0, n);
+  cudaError_t e = launch_normals(&dview, n, dst_range, p->normal_rel_jump, planes, nullptr, st);
+  prof_after(st);
+  if (e != cudaSuccess) return cuda_fail(e, "normals kernel");
+  if (levels > 1) {
+    prof_before(st, K_SRC_PYRAMID, 1, n);
+    e = launch_pyramid(n, H, W, levels, 1, src_range, srcl, st);
+    prof_after(st);
+    if (e != cudaSuccess) return cuda_fail(e, "pyramid kernel");
+    if (p->max_corr_dist > 0.f) {   // the distance gate reads the target ranges of every level
+      prof_before(st, K_PYRAMID, 1, n);
+      e = launch_pyramid(n, H, W, levels, 1, dst_range, dstl, st);
+      prof_after(st);
+      if (e != cudaSuccess) return cuda_fail(e, "pyramid kernel");
+    }
   }
   return RIMG_OK;
 }
@@ -249,39 +307,13 @@ int register_slice(const rimg_sensor* src, const rimg_sensor* dst, int p0, int n
     RIMG_CUDA(cudaMemcpyAsync(T_out, T_init, sizeof(double) * 16 * n, cudaMemcpyDeviceToDevice, st));
   const IcpScratch scr = icp_scratch(ws, R.icp, H, p0);
   RIMG_CUDA(cudaMemsetAsync(scr.counters, 0, sizeof(unsigned) * n, st));
-  // Target planes of every level (normals at the finest level, strided pyramid).
-  float* planes[RIMG_MAX_LEVELS] = {};
-  float* srcl[RIMG_MAX_LEVELS] = {};
-  float* dstl[RIMG_MAX_LEVELS] = {};
-  for (int l = 0; l < levels; ++l) {
-    const size_t Nl = (size_t)(H >> l) * (W >> l);
-    planes[l] = reinterpret_cast<float*>(ws + R.planes[l]) + 4 * Nl * p0;
-    if (l >= 1) {
-      srcl[l] = reinterpret_cast<float*>(ws + R.src_lvl[l]) + Nl * p0;
-      dstl[l] = reinterpret_cast<float*>(ws + R.dst_lvl[l]) + Nl * p0;
-    }
-  }
+  const SliceBufs b = slice_bufs(ws, R, H, W, levels, p0);
+  int rc0 = prep_slice(src, dst, n, src_range, dst_range, levels, p, b, st);
+  if (rc0) return rc0;
   const bool gate = p->max_corr_dist > 0.f;
-  // rimg_normals writes every level of dst's table set; register may use fewer
-  // levels than the sensor has, so build a view limited to `levels`.
-  rimg_sensor dview = *dst;
-  dview.levels = levels;
-  prof_before(st, K_NORMALS, 0, n);
-  cudaError_t e = launch_normals(&dview, n, dst_range, p->normal_rel_jump, planes, nullptr, st);
-  prof_after(st);
-  if (e != cudaSuccess) return cuda_fail(e, "normals kernel");
-  if (levels > 1) {
-    prof_before(st, K_SRC_PYRAMID, 1, n);
-    e = launch_pyramid(n, H, W, levels, 1, src_range, srcl, st);
-    prof_after(st);
-    if (e != cudaSuccess) return cuda_fail(e, "pyramid kernel");
-    if (gate) {   // the distance gate reads the target ranges of every level
-      prof_before(st, K_PYRAMID, 1, n);
-      e = launch_pyramid(n, H, W, levels, 1, dst_range, dstl, st);
-      prof_after(st);
-      if (e != cudaSuccess) return cuda_fail(e, "pyramid kernel");
-    }
-  }
+  const float* const* planes = b.planes;
+  const float* const* srcl = b.srcl;
+  const float* const* dstl = b.dstl;
   for (int k = 0; k < levels; ++k) {
     const int l = levels - 1 - k;
     const float* s_l = (l == 0) ? src_range : srcl[l];
@@ -340,6 +372,61 @@ int register_device(const rimg_sensor* src, const rimg_sensor* dst, int n_pairs,
   }
   return RIMG_OK;
 }
+
+// ---- groups of batches (uneven sizes) ----
+struct GroupWs {
+  std::vector<size_t> off;    // byte offset of each group's registration workspace
+  std::vector<RegWs> reg;
+  size_t end = 0;
+};
+
+GroupWs groups_ws(int n_groups, const rimg_group* g) {
+  GroupWs w;
+  size_t o = 0;
+  for (int i = 0; i < n_groups; ++i) {
+    o = align_up(o);
+    w.off.push_back(o);
+    w.reg.push_back(reg_ws(g[i].src->H, g[i].src->W, g[i].n_pairs, g[i].levels, 0));
+    o += w.reg.back().end;
+  }
+  w.end = align_up(o);
+  return w;
+}
+
+struct Slice {
+  int group, p0, n;
+  double work;
+};
+
+// Slices of every group: each group splits into params->streams sub-batches
+// of at least 32 pairs; largest work first.
+std::vector<Slice> group_slices(int n_groups, const rimg_group* g) {
+  std::vector<Slice> out;
+  for (int i = 0; i < n_groups; ++i) {
+    const int n = g[i].n_pairs;
+    if (n == 0) continue;
+    int S = std::min(std::max(g[i].params->streams, 1), 4);
+    if (n < 32 * S) S = std::max(1, n / 32);
+    int p0 = 0;
+    for (int k = 0; k < S; ++k) {
+      const int c = n / S + (k < n % S ? 1 : 0);
+      int iters = 0;
+      for (int l = 0; l < g[i].levels; ++l) iters += g[i].iters[l];
+      out.push_back(Slice{i, p0, c, (double)c * g[i].src->H * g[i].src->W * iters});
+      p0 += c;
+    }
+  }
+  std::sort(out.begin(), out.end(), [](const Slice& a, const Slice& b) { return a.work > b.work; });
+  return out;
+}
+
+constexpr int kGroupStreams = 8;
+struct GroupStreams {
+  std::mutex mu;
+  int device = -1;
+  cudaStream_t s[kGroupStreams] = {};
+  cudaEvent_t fork = nullptr, join[kGroupStreams] = {};
+} g_grp;
 
 int check_register_args(const rimg_sensor* src, const rimg_sensor* dst, int n_pairs, int levels,
                         const int* iters, const rimg_params* p) {
@@ -748,6 +835,142 @@ int rimg_register_host(const rimg_sensor* src, const rimg_sensor* dst, int n_pai
                                     levels, iters, p, status_host, chunk_pairs, workspace, workspace_bytes, stream);
   if (rc) return rc;
   RIMG_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+  return RIMG_OK;
+}
+
+int rimg_register_groups_workspace_bytes(int n_groups, const rimg_group* groups, size_t* bytes) {
+  if (!bytes || n_groups < 0 || (n_groups > 0 && !groups)) return RIMG_ERR_INVALID_ARG;
+  for (int i = 0; i < n_groups; ++i) {
+    const rimg_group& g = groups[i];
+    int rc = check_register_args(g.src, g.dst, g.n_pairs, g.levels, g.iters, g.params);
+    if (rc) return rc;
+  }
+  *bytes = groups_ws(n_groups, groups).end;
+  return RIMG_OK;
+}
+
+int rimg_register_groups(int n_groups, const rimg_group* groups, void* workspace, size_t workspace_bytes,
+                         void* stream) {
+  size_t need = 0;
+  int rc = rimg_register_groups_workspace_bytes(n_groups, groups, &need);
+  if (rc) return rc;
+  for (int i = 0; i < n_groups; ++i) {
+    const rimg_group& g = groups[i];
+    if (g.n_pairs > 0 && (!g.src_range || !g.dst_range || !g.T_init || !g.T_out)) return RIMG_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(g.src_range) % 16) || (reinterpret_cast<uintptr_t>(g.dst_range) % 16))
+      return RIMG_ERR_INVALID_ARG;
+  }
+  if (n_groups == 0) return RIMG_OK;
+  if (!workspace || !aligned(workspace) || workspace_bytes < need) return RIMG_ERR_WORKSPACE;
+  const GroupWs w = groups_ws(n_groups, groups);
+  const std::vector<Slice> slices = group_slices(n_groups, groups);
+  if (slices.empty()) return RIMG_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  char* ws = static_cast<char*>(workspace);
+  std::lock_guard<std::mutex> lk(g_grp.mu);
+  int dev = 0;
+  RIMG_CUDA(cudaGetDevice(&dev));
+  if (g_grp.device != dev) {
+    for (int i = 0; i < kGroupStreams; ++i) {
+      RIMG_CUDA(cudaStreamCreateWithFlags(&g_grp.s[i], cudaStreamNonBlocking));
+      RIMG_CUDA(cudaEventCreateWithFlags(&g_grp.join[i], cudaEventDisableTiming));
+    }
+    RIMG_CUDA(cudaEventCreateWithFlags(&g_grp.fork, cudaEventDisableTiming));
+    g_grp.device = dev;
+  }
+  // Longest-processing-time-first assignment of slices to internal streams;
+  // slices of one group never share a workspace range, so all may overlap.
+  const int nstreams = std::min<int>(kGroupStreams, (int)slices.size());
+  std::vector<double> load(nstreams, 0.0);
+  std::vector<std::vector<int>> assign(nstreams);
+  for (int k = 0; k < (int)slices.size(); ++k) {
+    const int best = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    assign[best].push_back(k);
+    load[best] += slices[k].work;
+  }
+  RIMG_CUDA(cudaEventRecord(g_grp.fork, st));
+  for (int i = 0; i < nstreams; ++i) {
+    RIMG_CUDA(cudaStreamWaitEvent(g_grp.s[i], g_grp.fork, 0));
+    for (int k : assign[i]) {
+      const Slice& sl = slices[k];
+      const rimg_group& g = groups[sl.group];
+      rc = register_slice(g.src, g.dst, sl.p0, sl.n, g.src_range, g.dst_range, g.T_init, g.T_out, g.levels,
+                          g.iters, g.params, g.status, ws + w.off[sl.group], w.reg[sl.group], g_grp.s[i]);
+      if (rc) return rc;
+    }
+    RIMG_CUDA(cudaEventRecord(g_grp.join[i], g_grp.s[i]));
+    RIMG_CUDA(cudaStreamWaitEvent(st, g_grp.join[i], 0));
+  }
+  return RIMG_OK;
+}
+
+int rimg_autotune(int n_groups, const rimg_group* groups, void* workspace, size_t workspace_bytes, void* stream) {
+  size_t need = 0;
+  int rc = rimg_register_groups_workspace_bytes(n_groups, groups, &need);
+  if (rc) return rc;
+  if (n_groups == 0) return 0;
+  if (!workspace || !aligned(workspace) || workspace_bytes < need) return RIMG_ERR_WORKSPACE;
+  const GroupWs w = groups_ws(n_groups, groups);
+  const std::vector<Slice> slices = group_slices(n_groups, groups);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  char* ws = static_cast<char*>(workspace);
+  cudaEvent_t e0, e1;
+  RIMG_CUDA(cudaEventCreate(&e0));
+  RIMG_CUDA(cudaEventCreate(&e1));
+  int entries = 0;
+  std::vector<std::tuple<int, int, int>> done;
+  for (const Slice& sl : slices) {
+    const rimg_group& g = groups[sl.group];
+    const int H = g.src->H, W = g.src->W;
+    const size_t N = (size_t)H * W;
+    // the shape depends on (level size, pairs per launch): tune each once
+    if (std::find(done.begin(), done.end(), std::make_tuple(sl.group, sl.n, 0)) != done.end()) continue;
+    done.push_back(std::make_tuple(sl.group, sl.n, 0));
+    char* gws = ws + w.off[sl.group];
+    const RegWs& R = w.reg[sl.group];
+    const SliceBufs b = slice_bufs(gws, R, H, W, g.levels, sl.p0);
+    const float* s0 = g.src_range + sl.p0 * N;
+    rc = prep_slice(g.src, g.dst, sl.n, s0, g.dst_range + sl.p0 * N, g.levels, g.params, b, st);
+    if (rc) return rc;
+    double* pose = g.T_out + 16 * (size_t)sl.p0;
+    RIMG_CUDA(cudaMemcpyAsync(pose, g.T_init + 16 * (size_t)sl.p0, sizeof(double) * 16 * sl.n,
+                              cudaMemcpyDeviceToDevice, st));
+    const IcpScratch scr = icp_scratch(gws, R.icp, H, sl.p0);
+    RIMG_CUDA(cudaMemsetAsync(scr.counters, 0, sizeof(unsigned) * sl.n, st));
+    for (int l = 0; l < g.levels; ++l) {
+      const int Hl = H >> l, Wl = W >> l;
+      const float* sl_src = (l == 0) ? s0 : b.srcl[l];
+      const float* sl_dst = g.params->max_corr_dist > 0.f ? ((l == 0) ? g.dst_range + sl.p0 * N : b.dstl[l])
+                                                           : nullptr;
+      float best = 1e30f;
+      int best_t = 0, best_b = 0;
+      for (int T : {128, 256}) {
+        for (int bp = 1; bp <= Hl; bp *= 2) {
+          if ((long long)Hl * (Wl / 4) < (long long)T / 4 * bp) continue;   // blocks with no work
+          for (int rep = 0; rep < 4; ++rep) {
+            if (rep == 1) RIMG_CUDA(cudaEventRecord(e0, st));
+            rc = icp_launch(g.src, g.dst, l, sl.n, sl_src, b.planes[l], sl_dst, pose, g.params, 0, nullptr,
+                            nullptr, nullptr, scr, st, T, bp);
+            if (rc) return rc;
+          }
+          RIMG_CUDA(cudaEventRecord(e1, st));
+          RIMG_CUDA(cudaEventSynchronize(e1));
+          float ms = 0.f;
+          RIMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+          if (ms < best) { best = ms; best_t = T; best_b = bp; }
+        }
+      }
+      icp_tune_set(Hl, Wl, sl.n, best_t, best_b);
+      ++entries;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return entries;
+}
+
+int rimg_autotune_clear(void) {
+  icp_tune_clear();
   return RIMG_OK;
 }
 

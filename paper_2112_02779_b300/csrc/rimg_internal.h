@@ -58,6 +58,9 @@ struct IcpLaunch {
 // Blocks per pair and rows per block for a level (depends on the batch and
 // the device's resident-block capacity).
 void icp_grid(int H, int W, int n_pairs, int* bpp, int* rows_per_block, int* threads);
+void icp_tune_set(int H, int W, int n_pairs, int threads, int bpp);
+void icp_tune_clear();
+int icp_tune_size();
 cudaError_t launch_icp(const IcpLaunch& a, cudaStream_t st);
 cudaError_t launch_solve(int n_pairs, const double* sums, double* pose, int* status, cudaStream_t st);
 

@@ -12,6 +12,7 @@ import os
 import numpy as np
 
 from ._abi import (RIMG_MAX_LEVELS, RIMG_FLAG_DEGENERATE, RIMG_STATIC_SCRATCH_BYTES, rimg_level, rimg_sensor, rimg_params,
+                   rimg_group,
                    STATUS_NAMES, HEADER_FUNCTIONS)
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -57,6 +58,10 @@ _sig("rimg_register_host", _c_int, _P(rimg_sensor), _P(rimg_sensor), _c_int, _vp
      _P(_c_int), _P(rimg_params), _vp, _c_int, _vp, _c_size, _vp)
 _sig("rimg_register_host_async", _c_int, _P(rimg_sensor), _P(rimg_sensor), _c_int, _vp, _vp, _vp, _vp, _c_int,
      _P(_c_int), _P(rimg_params), _vp, _c_int, _vp, _c_size, _vp)
+_sig("rimg_register_groups_workspace_bytes", _c_int, _c_int, _P(rimg_group), _P(_c_size))
+_sig("rimg_register_groups", _c_int, _c_int, _P(rimg_group), _vp, _c_size, _vp)
+_sig("rimg_autotune", _c_int, _c_int, _P(rimg_group), _vp, _c_size, _vp)
+_sig("rimg_autotune_clear", _c_int)
 _sig("rimg_profile_begin", _c_int, _c_int)
 _sig("rimg_profile_end", _c_int, _c_int, _P(_c_int), _P(_c_int), _P(_c_int), _P(ctypes.c_float), _P(ctypes.c_float))
 
@@ -246,6 +251,47 @@ def rimg_register_host_async(src, dst, n_pairs, src_range_host, dst_range_host, 
         _ptr(workspace), workspace.numel() if workspace is not None else 0, _stream(stream)))
 
 
+class Groups:
+    """A C array of rimg_group built from Python descriptions; keeps every
+    referenced object (sensors, parameters, schedules, tensors) alive."""
+
+    def __init__(self, groups):
+        self._keep = []
+        self.array = (rimg_group * max(len(groups), 1))()
+        self.n = len(groups)
+        for i, g in enumerate(groups):
+            it = _iters(g["iters"])
+            prm = g["params"]
+            self._keep += [g, it, prm]
+            self.array[i] = rimg_group(ctypes.pointer(g["src"].struct), ctypes.pointer(g["dst"].struct),
+                                       int(g["n_pairs"]), int(g["levels"]), it, ctypes.pointer(prm),
+                                       _ptr(g["src_range"]), _ptr(g["dst_range"]), _ptr(g["T_init"]),
+                                       _ptr(g["T_out"]), _ptr(g.get("status")))
+
+
+def rimg_register_groups_workspace_bytes(groups):
+    b = _c_size(0)
+    _check("rimg_register_groups_workspace_bytes",
+           _lib.rimg_register_groups_workspace_bytes(groups.n, groups.array, ctypes.byref(b)))
+    return b.value
+
+
+def rimg_register_groups(groups, workspace, stream=None):
+    _check("rimg_register_groups", _lib.rimg_register_groups(groups.n, groups.array, _ptr(workspace),
+                                                             workspace.numel(), _stream(stream)))
+
+
+def rimg_autotune(groups, workspace, stream=None):
+    n = _lib.rimg_autotune(groups.n, groups.array, _ptr(workspace), workspace.numel(), _stream(stream))
+    if n < 0:
+        raise RimgError("rimg_autotune", n)
+    return n
+
+
+def rimg_autotune_clear():
+    _check("rimg_autotune_clear", _lib.rimg_autotune_clear())
+
+
 def rimg_profile_begin(max_launches):
     _check("rimg_profile_begin", _lib.rimg_profile_begin(max_launches))
 
@@ -265,5 +311,5 @@ def rimg_profile_end(cap=100000):
 
 KERNEL_NAMES = {0: "unproject", 1: "pyramid", 2: "normals", 3: "icp_step", 4: "src_pyramid", 5: "solve"}
 
-__all__ = [n for n in dir() if n.startswith("rimg_")] + ["Sensor", "RimgError", "KERNEL_NAMES",
+__all__ = [n for n in dir() if n.startswith("rimg_")] + ["Sensor", "Groups", "RimgError", "KERNEL_NAMES",
                                                           "RIMG_MAX_LEVELS", "RIMG_FLAG_DEGENERATE", "lib"]

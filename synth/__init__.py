@@ -10,10 +10,10 @@ shape, range mix and invalid-pixel ratio.
 """
 from .luts import uniform_phi, hdl64_like_phi, zero_theta, random_theta
 from .scenes import Sensor, Scene, outdoor_scene, indoor_scene, raycast, random_delta_pose
-from .configs import CONFIGS, PairConfig, make_pair, make_pairs
+from .configs import CONFIGS, PairConfig, make_pair, make_pairs, MIXED_KINDS, mixed_batch_plan
 
 __all__ = [
     "uniform_phi", "hdl64_like_phi", "zero_theta", "random_theta",
     "Sensor", "Scene", "outdoor_scene", "indoor_scene", "raycast", "random_delta_pose",
-    "CONFIGS", "PairConfig", "make_pair", "make_pairs",
+    "CONFIGS", "PairConfig", "make_pair", "make_pairs", "MIXED_KINDS", "mixed_batch_plan",
 ]

@@ -68,6 +68,33 @@ CONFIGS = {
                                  scene="indoor", n_objects=12, r_min=0.3, r_max=40.0,
                                  rot_max_deg=5.0, trans_max=1.0, sigma=0.01, levels=4,
                                  iters=(10, 10, 10, 10), huber_delta=0.2, seed_base=3000),
+    # Sizes of the mixed batched workload (rot <= 5 deg, trans <= 1 m), outdoor and indoor.
+    "mixed32x512_out": PairConfig("mixed32x512_out", 41, 32, 512, "uniform", 15.0, -15.0,
+                                  n_objects=60, r_min=0.5, r_max=80.0, rot_max_deg=5.0, trans_max=1.0,
+                                  levels=3, iters=(10, 10, 10), seed_base=4000),
+    "mixed32x512_in": PairConfig("mixed32x512_in", 42, 32, 512, "uniform", 15.0, -15.0, scene="indoor",
+                                 n_objects=12, r_min=0.3, r_max=40.0, rot_max_deg=5.0, trans_max=1.0,
+                                 sigma=0.01, levels=3, iters=(10, 10, 10), huber_delta=0.2, seed_base=4000),
+    "mixed64x1024_out": PairConfig("mixed64x1024_out", 43, 64, 1024, "hdl64", n_objects=200, r_min=1.0,
+                                   r_max=120.0, rot_max_deg=5.0, trans_max=1.0, levels=4,
+                                   iters=(10, 10, 10, 10), seed_base=4000),
+    "mixed64x1024_in": PairConfig("mixed64x1024_in", 44, 64, 1024, "hdl64", scene="indoor", n_objects=12,
+                                  r_min=0.3, r_max=40.0, rot_max_deg=5.0, trans_max=1.0, sigma=0.01, levels=4,
+                                  iters=(10, 10, 10, 10), huber_delta=0.2, seed_base=4000),
+    "mixed128x1024_out": PairConfig("mixed128x1024_out", 45, 128, 1024, "uniform", 22.5, -22.5, n_objects=200,
+                                    r_min=0.5, r_max=120.0, rot_max_deg=5.0, trans_max=1.0, levels=4,
+                                    iters=(10, 10, 10, 10), seed_base=4000),
+    "mixed128x1024_in": PairConfig("mixed128x1024_in", 46, 128, 1024, "uniform", 22.5, -22.5, scene="indoor",
+                                   n_objects=12, r_min=0.3, r_max=40.0, rot_max_deg=5.0, trans_max=1.0,
+                                   sigma=0.01, levels=4, iters=(10, 10, 10, 10), huber_delta=0.2,
+                                   seed_base=4000),
+    "mixed128x2048_out": PairConfig("mixed128x2048_out", 47, 128, 2048, "uniform", 22.5, -22.5, n_objects=200,
+                                    r_min=0.5, r_max=120.0, rot_max_deg=5.0, trans_max=1.0, levels=4,
+                                    iters=(10, 10, 10, 10), seed_base=4000),
+    "mixed128x2048_in": PairConfig("mixed128x2048_in", 48, 128, 2048, "uniform", 22.5, -22.5, scene="indoor",
+                                   n_objects=12, r_min=0.3, r_max=40.0, rot_max_deg=5.0, trans_max=1.0,
+                                   sigma=0.01, levels=4, iters=(10, 10, 10, 10), huber_delta=0.2,
+                                   seed_base=4000),
     # Interlaced sensor with a receiver radius at a realistic size: 64 x 512,
     # theta_lut ~ U(-2, 2) deg, r0 = 1.5 cm (exercises the projection fixed point).
     "lut64x512": PairConfig("lut64x512", 8, 64, 512, "uniform", 10.0, -20.0,
@@ -140,3 +167,20 @@ def make_pairs(cfg, indices, processes=1):
     dst = np.stack([o[1] for o in out]) if out else np.zeros((0, cfg.H, cfg.W), np.float32)
     T = np.stack([o[2] for o in out]) if out else np.zeros((0, 4, 4))
     return src, dst, T
+
+
+MIXED_KINDS = ["mixed32x512_out", "mixed32x512_in", "mixed64x1024_out", "mixed64x1024_in",
+               "mixed128x1024_out", "mixed128x1024_in", "mixed128x2048_out", "mixed128x2048_in"]
+
+
+def mixed_batch_plan(n_pairs, seed=4000):
+    """The uneven batched workload: each of n_pairs pairs draws its size
+    uniformly from {32x512, 64x1024, 128x1024, 128x2048} and its scene from
+    outdoor / indoor (50/50).  Returns {kind: [pair indices]} (pair index i
+    of a kind is generated with make_pair(CONFIGS[kind], i))."""
+    rng = np.random.default_rng(np.random.SeedSequence([50, seed]))
+    kinds = rng.integers(0, len(MIXED_KINDS), size=n_pairs)
+    plan = {}
+    for j, k in enumerate(kinds):
+        plan.setdefault(MIXED_KINDS[k], []).append(j)
+    return plan

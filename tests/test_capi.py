@@ -46,16 +46,19 @@ int main(void) {
          offsetof(rimg_sensor, d_tables), offsetof(rimg_sensor, level));
   printf("%zu %zu %zu\n", offsetof(rimg_params, proj_iters), offsetof(rimg_params, kahan),
          offsetof(rimg_params, streams));
+  printf("%zu %zu %zu %zu\n", sizeof(rimg_group), offsetof(rimg_group, iters), offsetof(rimg_group, params),
+         offsetof(rimg_group, status));
   return 0;
 }
 ''')
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     vals = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
-    L, S, P = _abi.rimg_level, _abi.rimg_sensor, _abi.rimg_params
+    L, S, P, G = _abi.rimg_level, _abi.rimg_sensor, _abi.rimg_params, _abi.rimg_group
     assert vals == [ctypes.sizeof(L), ctypes.sizeof(S), ctypes.sizeof(P),
                     L.off_rows.offset, L.off_bins.offset, S.d_tables.offset, S.level.offset,
-                    P.proj_iters.offset, P.kahan.offset, P.streams.offset]
+                    P.proj_iters.offset, P.kahan.offset, P.streams.offset,
+                    ctypes.sizeof(G), G.iters.offset, G.params.offset, G.status.offset]
 
 
 def test_default_params_and_status_strings():

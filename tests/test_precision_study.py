@@ -1,0 +1,92 @@
+"""Precision study on the indoor 128 x 2048 workload: registration with
+Kahan-compensated FP32 accumulation of J^T W J / J^T W e against plain FP32
+accumulation, each compared pair by pair with the FP64 oracle.  On pairs whose
+4 x 10 schedule ends before the iteration has settled the oracle's final
+pose moves by ~1e-4 per step; those pairs are held to 1e-4 plus three of the
+oracle's own last steps, converged pairs to 1e-4.
+
+By default a sample of 12 pairs runs; RIMG_PRECISION_PAIRS=200 runs the full
+study.  With RIMG_REPORT_DIR set, a JSON report with every pair's errors is
+written there.  The oracle side runs in a spawn pool over the host cores."""
+import json
+import os
+import time
+
+import numpy as np
+import pytest
+
+from oracle import rimg_oracle as O
+from synth import CONFIGS, make_pairs
+from tests.gpu_common import f32, gpu_sensor, gpu_register, oracle_params
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+CFG = "indoor128x2048"
+
+
+def _oracle_one(args):
+    """Oracle pose and the size of its last Gauss-Newton step (how far the
+    trajectory still moves when the schedule ends)."""
+    src, dst, cfg_name = args
+    cfg = CONFIGS[cfg_name]
+    s = cfg.sensor()
+    sens = (s.phi_lut, s.theta_lut, s.r0)
+    T, _, hist = O.register(src, dst, sens, sens, np.eye(4), cfg.levels, cfg.iters, oracle_params(cfg),
+                            return_history=True)
+    return T, O.pose_error(hist[-1]["T_out"], hist[-1]["T_in"])
+
+
+def test_precision_kahan_vs_plain_fp32():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2112_02779_b300.rimg as R
+    cfg = CONFIGS[CFG]
+    n = int(os.environ.get("RIMG_PRECISION_PAIRS", "12"))
+    procs = max(1, min(64, (os.cpu_count() or 2) - 1))
+    src, dst, Tgt = make_pairs(cfg, range(n), processes=procs)
+    t0 = time.time()
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(procs) as pool:
+        out = pool.map(_oracle_one, [(src[i], dst[i], CFG) for i in range(n)])
+    To = [o[0] for o in out]
+    last = np.array([o[1] for o in out])
+    t_oracle = time.time() - t0
+    s = cfg.sensor()
+    sens = gpu_sensor(R, s, cfg.levels)
+    res = {}
+    for name, kahan in (("kahan", 1), ("plain", 0)):
+        params = R.rimg_default_params(huber_delta=cfg.huber_delta, kahan=kahan)
+        Tg, _ = gpu_register(R, torch, sens, src, dst, np.tile(np.eye(4), (n, 1, 1)), cfg.levels, cfg.iters, params)
+        res[name] = np.array([O.pose_error(Tg[i], To[i]) for i in range(n)])
+    gt = np.array([O.pose_error(To[i], Tgt[i]) for i in range(n)])
+    converged = (last[:, 0] < 1e-5) & (last[:, 1] < 1e-5)
+    summary = {
+        "workload": f"{CFG}: {cfg.H}x{cfg.W}, indoor rooms, sigma {cfg.sigma} m, {cfg.levels} levels x "
+                    f"{list(cfg.iters)}, delta {cfg.huber_delta} m",
+        "pairs": n, "oracle_seconds": t_oracle, "oracle_processes": procs,
+        **{f"{k}_{stat}_{c}": float(f(v[:, j])) for k, v in res.items()
+           for j, c in enumerate(("rot_rad", "trans_m"))
+           for stat, f in (("max", np.max), ("median", np.median), ("mean", np.mean))},
+        "oracle_vs_ground_truth_median_rot_rad": float(np.median(gt[:, 0])),
+        "oracle_vs_ground_truth_median_trans_m": float(np.median(gt[:, 1])),
+        "pairs_converged": int(converged.sum()),
+        **{f"{k}_pairs_over_1e-4": int(np.sum((v[:, 0] > 1e-4) | (v[:, 1] > 1e-4))) for k, v in res.items()},
+        **{f"{k}_converged_max_{c}": float(v[converged, j].max()) if converged.any() else None
+           for k, v in res.items() for j, c in enumerate(("rot_rad", "trans_m"))},
+    }
+    out = os.environ.get("RIMG_REPORT_DIR")
+    if out:
+        os.makedirs(out, exist_ok=True)
+        with open(os.path.join(out, "precision_study.json"), "w") as f:
+            json.dump({"summary": summary, "kahan": res["kahan"].tolist(), "plain": res["plain"].tolist(),
+                       "oracle_vs_gt": gt.tolist(), "oracle_last_step": last.tolist()}, f, indent=1)
+    print(json.dumps(summary))
+    # A pair whose schedule ends while the oracle's own iteration still moves
+    # by more than the bar is pinned only to about that step: the bar there
+    # is 1e-4 plus three last steps; converged pairs must meet 1e-4 exactly.
+    for k in ("kahan", "plain"):
+        bar = 1e-4 + 3 * last
+        assert np.all(res[k] <= bar), (k, res[k].max(0))
+        if converged.any():
+            assert res[k][converged].max() <= 1e-4, (k, res[k][converged].max(0))
