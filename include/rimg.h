@@ -337,6 +337,23 @@ int rimg_register_host_async(const rimg_sensor* src, const rimg_sensor* dst, int
                              size_t workspace_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Dense BF16 GEMM on the tcgen05 tensor cores (the contraction of the learned
+ * pose proposal's convolutions; the registration itself uses no tensor
+ * cores):  C[M x N] = A[M x K] * B[N x K]^T (+ bias[N]) (ReLU), FP32
+ * accumulation in tensor memory.  A and B are BF16, K-major (row i of A is K
+ * contiguous elements at A + i * lda), device, 16-byte aligned, lda and ldb
+ * multiples of 8 elements; K must be a multiple of 64 (zero-pad).  C: FP32
+ * row-major [M][ldc]; C_bf16 (nullable): a BF16 copy with the same leading
+ * dimension.  splits > 1 divides K into `splits` ranges (multiples of 64)
+ * computed by separate CTAs, each writing its own partial result at
+ * C + z * M * ldc (the caller sums them; bias, ReLU and C_bf16 must then be
+ * unset).  err (nullable, device int): set to 1 if a CTA gave up waiting for
+ * its tensor-core work (it then skips its epilogue).
+ * ------------------------------------------------------------------------- */
+int rimg_gemm_bf16(int M, int N, int K, const void* A, int lda, const void* B, int ldb, float* C, int ldc,
+                   void* C_bf16, const float* bias, int relu, int splits, int* err, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Launch timing (tracing).  rimg_profile_begin(max) makes subsequent library
  * launches on any stream record a CUDA event pair around each kernel (at most
  * `max` launches; later ones are not recorded).  rimg_profile_end waits for

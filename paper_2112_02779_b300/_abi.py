@@ -47,5 +47,5 @@ HEADER_FUNCTIONS = [
     "rimg_register_workspace_bytes", "rimg_register",
     "rimg_register_groups_workspace_bytes", "rimg_register_groups", "rimg_autotune", "rimg_autotune_clear",
     "rimg_register_host_workspace_bytes", "rimg_register_host", "rimg_register_host_async",
-    "rimg_profile_begin", "rimg_profile_end",
+    "rimg_gemm_bf16", "rimg_profile_begin", "rimg_profile_end",
 ]

@@ -974,6 +974,21 @@ int rimg_autotune_clear(void) {
   return RIMG_OK;
 }
 
+int rimg_gemm_bf16(int M, int N, int K, const void* A, int lda, const void* B, int ldb, float* C, int ldc,
+                   void* C_bf16, const float* bias, int relu, int splits, int* err, void* stream) {
+  if (M < 0 || N < 0 || K < 0 || splits < 1) return RIMG_ERR_INVALID_ARG;
+  if (M == 0 || N == 0) return RIMG_OK;
+  if (K % 64 || lda < K || ldb < K || lda % 8 || ldb % 8 || ldc < N) return RIMG_ERR_SIZE;
+  if (splits > 1 && (C_bf16 || bias || relu)) return RIMG_ERR_INVALID_ARG;
+  if (splits > std::max(1, K / 64)) return RIMG_ERR_INVALID_ARG;
+  if (!A || !B || !C) return RIMG_ERR_INVALID_ARG;
+  if ((reinterpret_cast<uintptr_t>(A) % 16) || (reinterpret_cast<uintptr_t>(B) % 16)) return RIMG_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = launch_gemm_bf16(M, N, K, A, lda, B, ldb, C, ldc, C_bf16, bias, relu, splits, err, st);
+  if (e != cudaSuccess) return cuda_fail(e, "tcgen05 gemm kernel");
+  return RIMG_OK;
+}
+
 int rimg_profile_begin(int max_launches) {
   if (max_launches < 0) return RIMG_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(g_prof.mu);

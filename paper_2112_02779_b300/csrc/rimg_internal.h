@@ -64,6 +64,9 @@ int icp_tune_size();
 cudaError_t launch_icp(const IcpLaunch& a, cudaStream_t st);
 cudaError_t launch_solve(int n_pairs, const double* sums, double* pose, int* status, cudaStream_t st);
 
+cudaError_t launch_gemm_bf16(int M, int N, int K, const void* A, int lda, const void* B, int ldb, float* C, int ldc,
+                             void* Cbf, const float* bias, int relu, int splits, int* err, cudaStream_t st);
+
 constexpr int kIcpThreads = 256;
 constexpr int kRed = 29;          // reduced quantities per pair
 constexpr int kRedStride = 32;    // floats per partial record

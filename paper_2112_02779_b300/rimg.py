@@ -62,6 +62,8 @@ _sig("rimg_register_groups_workspace_bytes", _c_int, _c_int, _P(rimg_group), _P(
 _sig("rimg_register_groups", _c_int, _c_int, _P(rimg_group), _vp, _c_size, _vp)
 _sig("rimg_autotune", _c_int, _c_int, _P(rimg_group), _vp, _c_size, _vp)
 _sig("rimg_autotune_clear", _c_int)
+_sig("rimg_gemm_bf16", _c_int, _c_int, _c_int, _c_int, _vp, _c_int, _vp, _c_int, _vp, _c_int, _vp, _vp, _c_int,
+     _c_int, _vp, _vp)
 _sig("rimg_profile_begin", _c_int, _c_int)
 _sig("rimg_profile_end", _c_int, _c_int, _P(_c_int), _P(_c_int), _P(_c_int), _P(ctypes.c_float), _P(ctypes.c_float))
 
@@ -290,6 +292,16 @@ def rimg_autotune(groups, workspace, stream=None):
 
 def rimg_autotune_clear():
     _check("rimg_autotune_clear", _lib.rimg_autotune_clear())
+
+
+def rimg_gemm_bf16(A, B, C, C_bf16=None, bias=None, relu=False, splits=1, err=None, stream=None):
+    """C = A @ B^T on the tcgen05 tensor cores; A [M, K] and B [N, K] bfloat16,
+    C float32 [M, N] (or [splits, M, N] with splits > 1)."""
+    M, K = A.shape
+    N = B.shape[0]
+    _check("rimg_gemm_bf16", _lib.rimg_gemm_bf16(M, N, K, _ptr(A), A.stride(0), _ptr(B), B.stride(0), _ptr(C),
+                                                 C.stride(-2), _ptr(C_bf16), _ptr(bias), int(relu), int(splits),
+                                                 _ptr(err), _stream(stream)))
 
 
 def rimg_profile_begin(max_launches):
