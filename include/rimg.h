@@ -258,6 +258,18 @@ int rimg_register(const rimg_sensor* src, const rimg_sensor* dst, int n_pairs,
                   double* T_out, int levels, const int* iters, const rimg_params* p, int* status,
                   void* workspace, size_t workspace_bytes, void* stream);
 
+/* The last Gauss-Newton step of the most recent rimg_register call on
+ * `workspace` (same sensors, n_pairs and levels): out32 float64 [n][32]
+ * device.  Entries 0-28 are that step's reduced sums in rimg_icp_step's
+ * out29 layout (21 entries of J^T W J, 6 of J^T W e, sum w e^2,
+ * correspondence count), evaluated at the pose before the update; 29 and 30
+ * are the sizes |omega| (rad) and |tau| (m) of the update xi = (omega, tau)
+ * that was applied, 31 is 1 if it was applied (0: degenerate, skipped).
+ * A caller judges convergence from them.  Ordered on `stream` after the
+ * registration if both use the same stream. */
+int rimg_register_last_sums(const rimg_sensor* src, const rimg_sensor* dst, int n_pairs, int levels,
+                            const void* workspace, size_t workspace_bytes, double* out32, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Uneven batches: several groups, each a batch of pairs of one sensor pair
  * (one image size) with its own schedule and parameters, registered in one
@@ -352,6 +364,87 @@ int rimg_register_host_async(const rimg_sensor* src, const rimg_sensor* dst, int
  * ------------------------------------------------------------------------- */
 int rimg_gemm_bf16(int M, int N, int K, const void* A, int lda, const void* B, int ldb, float* C, int ldc,
                    void* C_bf16, const float* bias, int relu, int splits, int* err, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Learned pose proposal (an extension: the paper starts Gauss-Newton from a
+ * given initial pose and names learned range-image features only as future
+ * work, Section 7).  A BF16 convolutional network reads the coarsest pyramid
+ * level (Section 4.1; every 8th row and column of a 64 x 1024 scan) of a
+ * source and a target scan and regresses T0, the init pose of rimg_register;
+ * the registration stays the judge of its result.
+ *
+ * Network: input [n][8][128][2] = (source, target) range * RIMG_CNN_RANGE_SCALE
+ * (0 for invalid ranges), BF16; five 3x3 stride-2 convolutions with ReLU,
+ * rows zero-padded, columns wrapped around (360 degrees of azimuth), channels
+ * 2 -> 32 -> 64 -> 64 -> 128 -> 128 (8x128 -> 4x64 -> 2x32 -> 1x16 -> 1x8 ->
+ * 1x4); a linear layer 512 -> 6 on the (w, c)-flattened activations gives
+ * p = (omega / RIMG_CNN_OMEGA_SCALE, t / RIMG_CNN_T_SCALE) and
+ * T0 = [Exp(omega), t] (Exp: Rodrigues).  BF16 operands, FP32 accumulation on
+ * the tcgen05 tensor cores (rimg_gemm_bf16's kernel), FP32 master weights.
+ *
+ * Parameters (FP32, rimg_cnn_param_count of them, in this order): for each
+ * convolution W [C_out][9 C_in] (column (kh * 3 + kw) * C_in + c) and
+ * b [C_out]; then the linear W [6][512] (column w * 128 + c) and b [6].
+ *
+ * State: one device buffer (256-byte aligned, rimg_cnn_state_bytes long)
+ * holding the master parameters (its first param_count floats), the Adam
+ * moments and BF16 copies of the weights.  Workspace: per batch size n,
+ * rimg_cnn_workspace_bytes(n), 256-byte aligned; one call at a time per
+ * workspace.
+ *
+ * Inputs: src_range, dst_range float32 [*][H][W] device with
+ * H = 8 * stride and W = 128 * stride (stride 8 reads the coarsest level of
+ * a 4-level 64 x 1024 pyramid straight from the full images; stride 1 reads
+ * stored 8 x 128 images).  index (nullable, device int32 [n]): pair i of the
+ * batch is image index[i] (and label index[i]); NULL means i.  T_label
+ * float64 [*][16]: the training target poses.  err (nullable, device int):
+ * set to 1 if a tensor-core wait timed out (that GEMM tile's output is then
+ * not written).  Sizes: 0 <= n <= RIMG_CNN_MAX_BATCH.
+ * ------------------------------------------------------------------------- */
+#define RIMG_CNN_IN_H 8
+#define RIMG_CNN_IN_W 128
+#define RIMG_CNN_RANGE_SCALE 0.03125f
+#define RIMG_CNN_OMEGA_SCALE 0.25
+#define RIMG_CNN_T_SCALE 3.0
+#define RIMG_CNN_MAX_BATCH 65536
+
+typedef struct rimg_adam {
+  float lr, beta1, beta2, eps;
+} rimg_adam;
+
+int rimg_cnn_param_count(size_t* n_params);
+int rimg_cnn_state_bytes(size_t* bytes);
+int rimg_cnn_workspace_bytes(int n, size_t* bytes);
+
+/* Seeded initialisation: He-uniform convolution weights U(+-sqrt(6 / fan_in)),
+ * linear weights U(+-0.1 sqrt(3 / 512)), zero biases, zero moments. */
+int rimg_cnn_init(void* state, size_t state_bytes, uint64_t seed, void* stream);
+
+/* Master parameters from `params` (device FP32 [param_count]; may be the
+ * state's own first floats), Adam moments cleared, BF16 copies rebuilt. */
+int rimg_cnn_load(void* state, size_t state_bytes, const float* params, void* stream);
+
+/* Inference: pred (nullable) float32 [n][6] network outputs p; T_out
+ * (nullable) float64 [n][16] proposals T0 = [Exp(0.25 p[0:3]), 3 p[3:6]]. */
+int rimg_propose(const void* state, int n, int H, int W, int stride, const float* src_range, const float* dst_range,
+                 const int32_t* index, float* pred, double* T_out, int* err, void* workspace, size_t workspace_bytes,
+                 void* stream);
+
+/* Loss and gradient without an update: loss (nullable, device double)
+ * = 1 / (2 n) sum_i |p_i - y_i|^2 with y = (Log R / 0.25, t / 3) of the
+ * label pose [R, t]; grad: device FP32 [param_count] in the parameter order;
+ * pred (nullable) as in rimg_propose.  Backpropagation treats the BF16
+ * roundings as identities. */
+int rimg_cnn_grad(const void* state, int n, int H, int W, int stride, const float* src_range, const float* dst_range,
+                  const int32_t* index, const double* T_label, double* loss, float* grad, float* pred, int* err,
+                  void* workspace, size_t workspace_bytes, void* stream);
+
+/* One training step: the gradient of rimg_cnn_grad, then Adam (step >= 1:
+ * bias corrections 1 - beta^step) on the master parameters and a rebuild of
+ * the BF16 copies. */
+int rimg_cnn_train_step(void* state, size_t state_bytes, int n, int H, int W, int stride, const float* src_range,
+                        const float* dst_range, const int32_t* index, const double* T_label, const rimg_adam* opt,
+                        int step, double* loss, int* err, void* workspace, size_t workspace_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Launch timing (tracing).  rimg_profile_begin(max) makes subsequent library

@@ -44,8 +44,22 @@ HEADER_FUNCTIONS = [
     "rimg_default_params", "rimg_status_string", "rimg_last_error",
     "rimg_sensor_table_bytes", "rimg_sensor_build", "rimg_unproject", "rimg_pyramid", "rimg_normals",
     "rimg_icp_workspace_bytes", "rimg_icp_step", "rimg_icp_step_static",
-    "rimg_register_workspace_bytes", "rimg_register",
+    "rimg_register_workspace_bytes", "rimg_register", "rimg_register_last_sums",
     "rimg_register_groups_workspace_bytes", "rimg_register_groups", "rimg_autotune", "rimg_autotune_clear",
     "rimg_register_host_workspace_bytes", "rimg_register_host", "rimg_register_host_async",
     "rimg_gemm_bf16", "rimg_profile_begin", "rimg_profile_end",
+    "rimg_cnn_param_count", "rimg_cnn_state_bytes", "rimg_cnn_workspace_bytes", "rimg_cnn_init", "rimg_cnn_load",
+    "rimg_propose", "rimg_cnn_grad", "rimg_cnn_train_step",
 ]
+
+# Learned pose proposal constants (rimg.h)
+RIMG_CNN_IN_H, RIMG_CNN_IN_W = 8, 128
+RIMG_CNN_RANGE_SCALE = 0.03125
+RIMG_CNN_OMEGA_SCALE = 0.25
+RIMG_CNN_T_SCALE = 3.0
+RIMG_CNN_MAX_BATCH = 65536
+
+
+class rimg_adam(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float)]

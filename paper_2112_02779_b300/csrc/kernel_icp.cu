@@ -445,12 +445,13 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS) k_icp(IcpLaunch a) {
 // The Gauss-Newton update of every pair from its FP64 sums: one thread per
 // pair (FP64 Cholesky-type solve of the 6x6 system and the SE(3) composition).
 // Kept out of k_icp so that no reduction block holds an SM slot through the
-// serial FP64 chain.
-__global__ void __launch_bounds__(32) k_solve(int n_pairs, const double* __restrict__ sums,
+// serial FP64 chain.  The pair's record keeps the size of the step in its
+// spare slots: [29] |omega| (rad), [30] |tau| (m), [31] 1 if applied.
+__global__ void __launch_bounds__(32) k_solve(int n_pairs, double* __restrict__ sums,
                                              double* __restrict__ pose, int* __restrict__ status) {
   const int pair = blockIdx.x * blockDim.x + threadIdx.x;
   if (pair >= n_pairs) return;
-  const double* t = sums + (long long)pair * kRedStride;
+  double* t = sums + (long long)pair * kRedStride;
   double Hm[6][6], g[6], x[6];
   int q = 0;
   for (int i = 0; i < 6; ++i)
@@ -464,12 +465,18 @@ __global__ void __launch_bounds__(32) k_solve(int n_pairs, const double* __restr
     for (int k = 0; k < 12; ++k) T[k] = P[k];
     se3_left_update(T, x);
     for (int k = 0; k < 12; ++k) P[k] = T[k];
-  } else if (status) {
-    status[pair] |= RIMG_FLAG_DEGENERATE;
+    t[29] = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+    t[30] = sqrt(x[3] * x[3] + x[4] * x[4] + x[5] * x[5]);
+    t[31] = 1.0;
+  } else {
+    t[29] = 0.0;
+    t[30] = 0.0;
+    t[31] = 0.0;
+    if (status) status[pair] |= RIMG_FLAG_DEGENERATE;
   }
 }
 
-cudaError_t launch_solve(int n_pairs, const double* sums, double* pose, int* status, cudaStream_t st) {
+cudaError_t launch_solve(int n_pairs, double* sums, double* pose, int* status, cudaStream_t st) {
   if (n_pairs == 0) return cudaSuccess;
   k_solve<<<(n_pairs + 31) / 32, 32, 0, st>>>(n_pairs, sums, pose, status);
   return cudaGetLastError();

@@ -746,6 +746,23 @@ int rimg_register(const rimg_sensor* src, const rimg_sensor* dst, int n_pairs, c
                          static_cast<char*>(workspace), R, static_cast<cudaStream_t>(stream));
 }
 
+int rimg_register_last_sums(const rimg_sensor* src, const rimg_sensor* dst, int n_pairs, int levels,
+                            const void* workspace, size_t workspace_bytes, double* out32, void* stream) {
+  int rc = check_sensor(src);
+  if (rc) return rc;
+  if ((rc = check_sensor(dst))) return rc;
+  if (src->H != dst->H || src->W != dst->W) return RIMG_ERR_MISMATCH;
+  if (n_pairs < 0 || levels < 1 || levels > src->levels || levels > dst->levels) return RIMG_ERR_INVALID_ARG;
+  if (n_pairs == 0) return RIMG_OK;
+  if (!out32 || !workspace) return RIMG_ERR_INVALID_ARG;
+  const RegWs R = reg_ws(src->H, src->W, n_pairs, levels, 0);
+  if (!aligned(workspace) || workspace_bytes < R.end) return RIMG_ERR_WORKSPACE;
+  RIMG_CUDA(cudaMemcpyAsync(out32, static_cast<const char*>(workspace) + R.icp.sums,
+                            sizeof(double) * kRedStride * (size_t)n_pairs, cudaMemcpyDeviceToDevice,
+                            static_cast<cudaStream_t>(stream)));
+  return RIMG_OK;
+}
+
 int rimg_register_host_workspace_bytes(const rimg_sensor* src, const rimg_sensor* dst, int n_pairs, int levels,
                                        int chunk_pairs, size_t* bytes) {
   if (!bytes) return RIMG_ERR_INVALID_ARG;
@@ -1030,3 +1047,9 @@ int rimg_profile_end(int cap, int* kernel_id, int* level, int* n_pairs, float* s
 }
 
 }  // extern "C"
+
+namespace rimg {
+// Records a failed CUDA call for rimg_last_error (used by the other
+// translation units' entry points).
+int record_cuda_error(cudaError_t e, const char* where) { return cuda_fail(e, where); }
+}  // namespace rimg

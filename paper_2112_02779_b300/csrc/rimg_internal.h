@@ -62,10 +62,13 @@ void icp_tune_set(int H, int W, int n_pairs, int threads, int bpp);
 void icp_tune_clear();
 int icp_tune_size();
 cudaError_t launch_icp(const IcpLaunch& a, cudaStream_t st);
-cudaError_t launch_solve(int n_pairs, const double* sums, double* pose, int* status, cudaStream_t st);
+cudaError_t launch_solve(int n_pairs, double* sums, double* pose, int* status, cudaStream_t st);
 
 cudaError_t launch_gemm_bf16(int M, int N, int K, const void* A, int lda, const void* B, int ldb, float* C, int ldc,
                              void* Cbf, const float* bias, int relu, int splits, int* err, cudaStream_t st);
+
+// Records a failed CUDA call for rimg_last_error; returns RIMG_ERR_CUDA.
+int record_cuda_error(cudaError_t e, const char* where);
 
 constexpr int kIcpThreads = 256;
 constexpr int kRed = 29;          // reduced quantities per pair

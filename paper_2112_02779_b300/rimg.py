@@ -12,7 +12,7 @@ import os
 import numpy as np
 
 from ._abi import (RIMG_MAX_LEVELS, RIMG_FLAG_DEGENERATE, RIMG_STATIC_SCRATCH_BYTES, rimg_level, rimg_sensor, rimg_params,
-                   rimg_group,
+                   rimg_group, rimg_adam, RIMG_CNN_IN_H, RIMG_CNN_IN_W, RIMG_CNN_MAX_BATCH,
                    STATUS_NAMES, HEADER_FUNCTIONS)
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -52,6 +52,7 @@ _sig("rimg_icp_step_static", _c_int, _P(rimg_sensor), _P(rimg_sensor), _c_int, _
 _sig("rimg_register_workspace_bytes", _c_int, _P(rimg_sensor), _P(rimg_sensor), _c_int, _c_int, _P(_c_size))
 _sig("rimg_register", _c_int, _P(rimg_sensor), _P(rimg_sensor), _c_int, _vp, _vp, _vp, _vp, _c_int,
      _P(_c_int), _P(rimg_params), _vp, _vp, _c_size, _vp)
+_sig("rimg_register_last_sums", _c_int, _P(rimg_sensor), _P(rimg_sensor), _c_int, _c_int, _vp, _c_size, _vp, _vp)
 _sig("rimg_register_host_workspace_bytes", _c_int, _P(rimg_sensor), _P(rimg_sensor), _c_int, _c_int,
      _c_int, _P(_c_size))
 _sig("rimg_register_host", _c_int, _P(rimg_sensor), _P(rimg_sensor), _c_int, _vp, _vp, _vp, _vp, _c_int,
@@ -64,6 +65,16 @@ _sig("rimg_autotune", _c_int, _c_int, _P(rimg_group), _vp, _c_size, _vp)
 _sig("rimg_autotune_clear", _c_int)
 _sig("rimg_gemm_bf16", _c_int, _c_int, _c_int, _c_int, _vp, _c_int, _vp, _c_int, _vp, _c_int, _vp, _vp, _c_int,
      _c_int, _vp, _vp)
+_sig("rimg_cnn_param_count", _c_int, _P(_c_size))
+_sig("rimg_cnn_state_bytes", _c_int, _P(_c_size))
+_sig("rimg_cnn_workspace_bytes", _c_int, _c_int, _P(_c_size))
+_sig("rimg_cnn_init", _c_int, _vp, _c_size, ctypes.c_uint64, _vp)
+_sig("rimg_cnn_load", _c_int, _vp, _c_size, _vp, _vp)
+_sig("rimg_propose", _c_int, _vp, _c_int, _c_int, _c_int, _c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _c_size, _vp)
+_sig("rimg_cnn_grad", _c_int, _vp, _c_int, _c_int, _c_int, _c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+     _c_size, _vp)
+_sig("rimg_cnn_train_step", _c_int, _vp, _c_size, _c_int, _c_int, _c_int, _c_int, _vp, _vp, _vp, _vp,
+     _P(rimg_adam), _c_int, _vp, _vp, _vp, _c_size, _vp)
 _sig("rimg_profile_begin", _c_int, _c_int)
 _sig("rimg_profile_end", _c_int, _c_int, _P(_c_int), _P(_c_int), _P(_c_int), _P(ctypes.c_float), _P(ctypes.c_float))
 
@@ -227,6 +238,11 @@ def rimg_register(src, dst, n_pairs, src_range, dst_range, T_init, T_out, levels
         workspace.numel() if workspace is not None else 0, _stream(stream)))
 
 
+def rimg_register_last_sums(src, dst, n_pairs, levels, workspace, out32, stream=None):
+    _check("rimg_register_last_sums", _lib.rimg_register_last_sums(
+        src.ref(), dst.ref(), n_pairs, levels, _ptr(workspace), workspace.numel(), _ptr(out32), _stream(stream)))
+
+
 def rimg_register_host_workspace_bytes(src, dst, n_pairs, levels, chunk_pairs=0):
     b = _c_size(0)
     _check("rimg_register_host_workspace_bytes", _lib.rimg_register_host_workspace_bytes(
@@ -304,6 +320,112 @@ def rimg_gemm_bf16(A, B, C, C_bf16=None, bias=None, relu=False, splits=1, err=No
                                                  _ptr(err), _stream(stream)))
 
 
+# ---------------------------------------------------------------------------
+# Learned pose proposal
+
+def rimg_cnn_param_count():
+    b = _c_size(0)
+    _check("rimg_cnn_param_count", _lib.rimg_cnn_param_count(ctypes.byref(b)))
+    return b.value
+
+
+def rimg_cnn_state_bytes():
+    b = _c_size(0)
+    _check("rimg_cnn_state_bytes", _lib.rimg_cnn_state_bytes(ctypes.byref(b)))
+    return b.value
+
+
+def rimg_cnn_workspace_bytes(n):
+    b = _c_size(0)
+    _check("rimg_cnn_workspace_bytes", _lib.rimg_cnn_workspace_bytes(int(n), ctypes.byref(b)))
+    return b.value
+
+
+def _images(src, dst):
+    H, W = src.shape[-2], src.shape[-1]
+    if dst.shape[-2:] != src.shape[-2:]:
+        raise ValueError("source and target images differ in size")
+    stride = H // RIMG_CNN_IN_H
+    return H, W, stride
+
+
+class ProposalNet:
+    """Device state of the proposal network (master FP32 parameters, Adam
+    moments, BF16 weight copies) and per-batch-size workspaces."""
+
+    def __init__(self, seed=None, params=None, device="cuda"):
+        import torch
+        self.n_params = rimg_cnn_param_count()
+        self.state = torch.zeros(rimg_cnn_state_bytes(), dtype=torch.uint8, device=device)
+        self._ws = {}
+        self.err = torch.zeros(1, dtype=torch.int32, device=device)
+        if params is not None:
+            self.load(params)
+        else:
+            self.init(0 if seed is None else seed)
+
+    @property
+    def params(self):
+        """The master parameters (a float32 view into the state)."""
+        import torch
+        return self.state[:4 * self.n_params].view(torch.float32)
+
+    def init(self, seed, stream=None):
+        rimg_cnn_init(self.state, seed, stream)
+
+    def load(self, params, stream=None):
+        rimg_cnn_load(self.state, params, stream)
+
+    def workspace(self, n):
+        import torch
+        ws = self._ws.get(n)
+        if ws is None:
+            ws = torch.empty(rimg_cnn_workspace_bytes(n), dtype=torch.uint8, device=self.state.device)
+            self._ws[n] = ws
+        return ws
+
+
+def rimg_cnn_init(state, seed, stream=None):
+    _check("rimg_cnn_init", _lib.rimg_cnn_init(_ptr(state), state.numel(), int(seed) & (2 ** 64 - 1),
+                                               _stream(stream)))
+
+
+def rimg_cnn_load(state, params, stream=None):
+    _check("rimg_cnn_load", _lib.rimg_cnn_load(_ptr(state), state.numel(), _ptr(params), _stream(stream)))
+
+
+def rimg_propose(net, src, dst, n=None, index=None, pred=None, T_out=None, workspace=None, stream=None):
+    """Proposals for n pairs: src, dst float32 [*, 8 s, 128 s] device images
+    (s = 8 for 64 x 1024 scans); index (int32 [n]) picks the pairs."""
+    H, W, stride = _images(src, dst)
+    n = (index.numel() if index is not None else src.shape[0]) if n is None else n
+    ws = workspace if workspace is not None else net.workspace(n)
+    _check("rimg_propose", _lib.rimg_propose(_ptr(net.state), n, H, W, stride, _ptr(src), _ptr(dst), _ptr(index),
+                                             _ptr(pred), _ptr(T_out), _ptr(net.err), _ptr(ws), ws.numel(),
+                                             _stream(stream)))
+
+
+def rimg_cnn_grad(net, src, dst, T_label, grad, n=None, index=None, loss=None, pred=None, workspace=None,
+                  stream=None):
+    H, W, stride = _images(src, dst)
+    n = (index.numel() if index is not None else src.shape[0]) if n is None else n
+    ws = workspace if workspace is not None else net.workspace(n)
+    _check("rimg_cnn_grad", _lib.rimg_cnn_grad(_ptr(net.state), n, H, W, stride, _ptr(src), _ptr(dst), _ptr(index),
+                                               _ptr(T_label), _ptr(loss), _ptr(grad), _ptr(pred), _ptr(net.err),
+                                               _ptr(ws), ws.numel(), _stream(stream)))
+
+
+def rimg_cnn_train_step(net, src, dst, T_label, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, n=None,
+                        index=None, loss=None, workspace=None, stream=None):
+    H, W, stride = _images(src, dst)
+    n = (index.numel() if index is not None else src.shape[0]) if n is None else n
+    ws = workspace if workspace is not None else net.workspace(n)
+    opt = rimg_adam(lr, beta1, beta2, eps)
+    _check("rimg_cnn_train_step", _lib.rimg_cnn_train_step(
+        _ptr(net.state), net.state.numel(), n, H, W, stride, _ptr(src), _ptr(dst), _ptr(index), _ptr(T_label),
+        ctypes.byref(opt), int(step), _ptr(loss), _ptr(net.err), _ptr(ws), ws.numel(), _stream(stream)))
+
+
 def rimg_profile_begin(max_launches):
     _check("rimg_profile_begin", _lib.rimg_profile_begin(max_launches))
 
@@ -323,5 +445,5 @@ def rimg_profile_end(cap=100000):
 
 KERNEL_NAMES = {0: "unproject", 1: "pyramid", 2: "normals", 3: "icp_step", 4: "src_pyramid", 5: "solve"}
 
-__all__ = [n for n in dir() if n.startswith("rimg_")] + ["Sensor", "Groups", "RimgError", "KERNEL_NAMES",
+__all__ = [n for n in dir() if n.startswith("rimg_")] + ["Sensor", "Groups", "ProposalNet", "RimgError", "KERNEL_NAMES",
                                                           "RIMG_MAX_LEVELS", "RIMG_FLAG_DEGENERATE", "lib"]

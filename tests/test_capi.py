@@ -119,3 +119,30 @@ def test_entry_points_reject_null_and_bad_arguments():
     bad = R.rimg_default_params(normal_rel_jump=0.7)
     assert lib.rimg_normals(None, 1, None, ctypes.byref(bad), None, None, None) == -1
     assert lib.rimg_profile_begin(-1) == -1
+
+
+def test_cnn_entry_points_check_arguments_on_the_host():
+    lib = R.lib()
+    n = ctypes.c_size_t()
+    assert lib.rimg_cnn_param_count(ctypes.byref(n)) == 0 and n.value == 280550
+    assert lib.rimg_cnn_state_bytes(ctypes.byref(n)) == 0 and n.value >= 3 * 4 * 280550
+    assert lib.rimg_cnn_workspace_bytes(-1, ctypes.byref(n)) == -1
+    assert lib.rimg_cnn_workspace_bytes(_abi.RIMG_CNN_MAX_BATCH + 1, ctypes.byref(n)) == -1
+    assert lib.rimg_cnn_workspace_bytes(64, ctypes.byref(n)) == 0 and n.value > 0
+    fake = 1 << 20                                    # never dereferenced: the checks come first
+    # state misaligned / too small
+    assert lib.rimg_cnn_init(fake + 4, 1 << 30, 1, None) == -4
+    assert lib.rimg_cnn_init(fake, 16, 1, None) == -4
+    # image size must be 8 s x 128 s
+    assert lib.rimg_propose(fake, 4, 64, 1000, 8, fake, fake, None, None, None, None, fake, 1 << 40, None) == -3
+    assert lib.rimg_propose(fake, 4, 64, 1024, 0, fake, fake, None, None, None, None, fake, 1 << 40, None) == -1
+    # workspace too small
+    assert lib.rimg_propose(fake, 4, 64, 1024, 8, fake, fake, None, None, None, None, fake, 16, None) == -4
+    # n = 0 is a no-op
+    assert lib.rimg_propose(fake, 0, 8, 128, 1, None, None, None, None, None, None, None, 0, None) == 0
+    opt = _abi.rimg_adam(1e-3, 0.9, 1.5, 1e-8)     # beta2 >= 1
+    assert lib.rimg_cnn_train_step(fake, 1 << 30, 4, 8, 128, 1, fake, fake, None, fake, ctypes.byref(opt), 1, None,
+                                   None, fake, 1 << 40, None) == -1
+    opt = _abi.rimg_adam(1e-3, 0.9, 0.999, 1e-8)
+    assert lib.rimg_cnn_train_step(fake, 1 << 30, 4, 8, 128, 1, fake, fake, None, fake, ctypes.byref(opt), 0, None,
+                                   None, fake, 1 << 40, None) == -1

@@ -519,3 +519,35 @@ def test_autotune_keeps_results(R):
         for i in range(len(a)):
             eR, et = O.pose_error(a[i], b[i])
             assert eR <= 1e-4 and et <= 1e-4
+
+
+def test_register_last_sums_record_the_final_step(R):
+    """rimg_register_last_sums: the final step's sums (at the pose it started
+    from) and the size of the update it applied, against the oracle's
+    Gauss-Newton step from the same pose."""
+    cfg = CONFIGS["pair32x512"]
+    pair = make_pair(cfg, 3)
+    s = pair["sensor"]
+    sens = gpu_sensor(R, s, 1)
+    params = R.rimg_default_params(huber_delta=cfg.huber_delta)
+    T = O.se3_exp(np.array([2e-3, -1e-3, 3e-3, 0.02, -0.01, 0.015])) @ pair["T_gt"]
+    src = torch.from_numpy(pair["src_range"])[None].cuda()
+    dst = torch.from_numpy(pair["dst_range"])[None].cuda()
+    T0 = torch.from_numpy(T.reshape(1, 16).copy()).cuda()
+    T1 = torch.empty_like(T0)
+    ws = torch.empty(R.rimg_register_workspace_bytes(sens, sens, 1, 1), dtype=torch.uint8, device="cuda")
+    R.rimg_register(sens, sens, 1, src, dst, T0, T1, 1, [1], params, None, ws)
+    rec = torch.zeros((1, 32), dtype=torch.float64, device="cuda")
+    R.rimg_register_last_sums(sens, sens, 1, 1, ws, rec)
+    torch.cuda.synchronize()
+    rec = rec[0].cpu().numpy()
+    tgt = O.Target(pair["dst_range"], s.phi_lut, s.theta_lut, s.r0, 1, f32(0.1))
+    P, sv = O.source_points(pair["src_range"], s.phi_lut, s.theta_lut, s.r0, 0)
+    rng_l, n_l, nv_l, ph, th = tgt.level(0)
+    terms = O.icp_terms(P, sv, T, rng_l, n_l, nv_l, ph, th, s.r0, f32(params.huber_delta), 0.0,
+                        dst_n_margin=tgt.nmargin[0])
+    n_mis = int(np.sum(terms["near_tie"]))
+    assert np.all(np.abs(rec[:29] - O.pack29(terms)) <= _sum_bounds(terms, n_mis) + 1e-9)
+    xi, ok = O.cholesky_solve(terms["H"], terms["g"])
+    assert ok and rec[31] == 1.0
+    np.testing.assert_allclose(rec[29:31], [np.linalg.norm(xi[:3]), np.linalg.norm(xi[3:])], rtol=1e-3, atol=1e-9)
