@@ -95,6 +95,11 @@ CONFIGS = {
                                    n_objects=12, r_min=0.3, r_max=40.0, rot_max_deg=5.0, trans_max=1.0,
                                    sigma=0.01, levels=4, iters=(10, 10, 10, 10), huber_delta=0.2,
                                    seed_base=4000),
+    # Learned-proposal workload: the headline sensor and scenes with large
+    # motions (rot <= 15 deg, trans <= 3 m); cast on the GPU by synth.gpu.
+    "learn64x1024": PairConfig("learn64x1024", 5, 64, 1024, "hdl64",
+                               n_objects=200, r_min=1.0, r_max=120.0, rot_max_deg=15.0,
+                               trans_max=3.0, levels=4, iters=(10, 10, 10, 10), seed_base=5000),
     # Interlaced sensor with a receiver radius at a realistic size: 64 x 512,
     # theta_lut ~ U(-2, 2) deg, r0 = 1.5 cm (exercises the projection fixed point).
     "lut64x512": PairConfig("lut64x512", 8, 64, 512, "uniform", 10.0, -20.0,
