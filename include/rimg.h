@@ -349,6 +349,36 @@ int rimg_register_host_async(const rimg_sensor* src, const rimg_sensor* dst, int
                              size_t workspace_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Projective SDF integration, Section 4.2 (Eq. 8-10), on a dense voxel grid.
+ *
+ * For each voxel centre x = origin + voxel * (i + 1/2, j + 1/2, k + 1/2) and
+ * each scan s: [u v r] = Pi(R_s x + t_s) at pyramid level `level` (Eq. 8; the
+ * projection of rimg_icp_step), and, when the point is inside the vertical
+ * field of view and the scan's range at (u, v) is valid, the signed distance
+ * along the ray d_s = range(u, v) - r (Eq. 9).  With trunc > 0 a scan with
+ * d_s < -trunc does not observe the voxel (it lies behind the surface) and
+ * d_s is clipped to trunc; trunc <= 0 keeps Eq. 9 as is.  The observations are
+ * merged into the voxel's least-squares estimate (Eq. 10) incrementally:
+ * sdf <- (sdf * weight + sum_s d_s) / (weight + count), weight += count.
+ *
+ * range_l: float32 [n_scans][H_l][W_l] device (level-l images, e.g. from
+ * rimg_pyramid).  T_world_to_sensor: float64 [n_scans][16] device, mapping
+ * world points into each scan's sensor frame.  sdf, weight: float32
+ * [nz][ny][nx] device (x fastest), read and updated in place (start from
+ * zeros).  p (nullable): only proj_iters is used.  n_scans = 0 or an empty
+ * grid is a no-op.
+ * ------------------------------------------------------------------------- */
+typedef struct rimg_grid {
+  int nx, ny, nz;
+  float voxel;              /* edge length, > 0 */
+  float origin[3];          /* world position of the outer corner of voxel (0, 0, 0) */
+} rimg_grid;
+
+int rimg_sdf_integrate(const rimg_sensor* sensor, int level, int n_scans, const float* range_l,
+                       const double* T_world_to_sensor, const rimg_grid* grid, float trunc, float* sdf,
+                       float* weight, const rimg_params* p, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Dense BF16 GEMM on the tcgen05 tensor cores (the contraction of the learned
  * pose proposal's convolutions; the registration itself uses no tensor
  * cores):  C[M x N] = A[M x K] * B[N x K]^T (+ bias[N]) (ReLU), FP32
@@ -457,7 +487,7 @@ int rimg_cnn_train_step(void* state, size_t state_bytes, int n, int H, int W, in
  * caller take the union of intervals.
  * Kernel ids: 0 unproject, 1 pyramid, 2 normals (+ plane pyramid),
  * 3 icp step (association + reduction), 4 source-range pyramid, 5 FP64
- * solve + pose update.  Not for use during stream capture.
+ * solve + pose update, 6 SDF integration.  Not for use during stream capture.
  * ------------------------------------------------------------------------- */
 int rimg_profile_begin(int max_launches);
 int rimg_profile_end(int cap, int* kernel_id, int* level, int* n_pairs, float* start_ms, float* ms);

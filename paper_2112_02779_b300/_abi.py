@@ -47,7 +47,7 @@ HEADER_FUNCTIONS = [
     "rimg_register_workspace_bytes", "rimg_register", "rimg_register_last_sums",
     "rimg_register_groups_workspace_bytes", "rimg_register_groups", "rimg_autotune", "rimg_autotune_clear",
     "rimg_register_host_workspace_bytes", "rimg_register_host", "rimg_register_host_async",
-    "rimg_gemm_bf16", "rimg_profile_begin", "rimg_profile_end",
+    "rimg_gemm_bf16", "rimg_profile_begin", "rimg_profile_end", "rimg_sdf_integrate",
     "rimg_cnn_param_count", "rimg_cnn_state_bytes", "rimg_cnn_workspace_bytes", "rimg_cnn_init", "rimg_cnn_load",
     "rimg_propose", "rimg_cnn_grad", "rimg_cnn_train_step",
 ]
@@ -58,6 +58,11 @@ RIMG_CNN_RANGE_SCALE = 0.03125
 RIMG_CNN_OMEGA_SCALE = 0.25
 RIMG_CNN_T_SCALE = 3.0
 RIMG_CNN_MAX_BATCH = 65536
+
+
+class rimg_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("voxel", ctypes.c_float),
+                ("origin", ctypes.c_float * 3)]
 
 
 class rimg_adam(ctypes.Structure):

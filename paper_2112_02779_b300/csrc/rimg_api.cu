@@ -645,6 +645,34 @@ int rimg_unproject(const rimg_sensor* s, int level, int n_images, const float* r
   return RIMG_OK;
 }
 
+int rimg_sdf_integrate(const rimg_sensor* s, int level, int n_scans, const float* range_l,
+                       const double* T_world_to_sensor, const rimg_grid* grid, float trunc, float* sdf,
+                       float* weight, const rimg_params* p, void* stream) {
+  int rc = check_sensor(s);
+  if (rc) return rc;
+  if (level < 0 || level >= s->levels || n_scans < 0 || !grid) return RIMG_ERR_INVALID_ARG;
+  if (grid->nx < 0 || grid->ny < 0 || grid->nz < 0) return RIMG_ERR_INVALID_ARG;
+  if (!(grid->voxel > 0.f) || !std::isfinite(grid->voxel) || !std::isfinite(trunc)) return RIMG_ERR_INVALID_ARG;
+  for (int a = 0; a < 3; ++a)
+    if (!std::isfinite(grid->origin[a])) return RIMG_ERR_INVALID_ARG;
+  if ((long long)grid->nx * grid->ny * grid->nz > ((long long)1 << 40)) return RIMG_ERR_SIZE;
+  if (p && (rc = check_params(p))) return rc;
+  const long long n_vox = (long long)grid->nx * grid->ny * grid->nz;
+  if (n_scans == 0 || n_vox == 0) return RIMG_OK;
+  if (!range_l || !T_world_to_sensor || !sdf || !weight) return RIMG_ERR_INVALID_ARG;
+  rimg_params d;
+  rimg_default_params(&d);
+  const int iters = p ? p->proj_iters : d.proj_iters;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  prof_before(st, K_SDF, level, n_scans);
+  cudaError_t e = launch_sdf(dev_level(s, level), n_scans, range_l, T_world_to_sensor, grid->nx, grid->ny, grid->nz,
+                             grid->origin[0], grid->origin[1], grid->origin[2], grid->voxel, trunc, iters, sdf,
+                             weight, st);
+  prof_after(st);
+  if (e != cudaSuccess) return cuda_fail(e, "sdf kernel");
+  return RIMG_OK;
+}
+
 int rimg_pyramid(int n_images, int H, int W, int levels, int channels, const float* in,
                  float* const* out_levels, void* stream) {
   if (n_images < 0 || H <= 0 || W <= 0 || levels < 1 || levels > RIMG_MAX_LEVELS) return RIMG_ERR_INVALID_ARG;

@@ -79,14 +79,18 @@ __device__ __forceinline__ int wrap_col(float uc, int W) {
 }
 
 // Pi (Section 3.2) of point x into level L.  Returns true when the point lies
-// inside the vertical field of view; (u, v) are always valid indices.
+// inside the vertical field of view; (u, v) are always valid indices and r is
+// the point's range from the receiver (|x - o| with the receiver offset o of
+// the last fixed-point step).
 template <bool R0>
-__device__ __forceinline__ bool project_px(const DevLevel& L, float3 x, int proj_iters, int& u,
-                                           int& v) {
+__device__ __forceinline__ bool project_px(const DevLevel& L, float3 x, int proj_iters, int& u, int& v,
+                                           float& r) {
   float s, uc;
   if (!R0) {
     const float n2 = fmaf(x.x, x.x, fmaf(x.y, x.y, x.z * x.z));
-    s = x.z * rsqrtf(n2);
+    const float inv = rsqrtf(n2);
+    s = x.z * inv;
+    r = n2 * inv;
     v = row_from_sin(L, s);
     uc = atan2_poly(x.y, x.x) * L.w_over_2pi;
     if (L.has_theta) uc -= __ldg(L.thu + v);
@@ -94,6 +98,7 @@ __device__ __forceinline__ bool project_px(const DevLevel& L, float3 x, int proj
     // receiver-offset fixed point on the column angle 2 pi u_c / W
     uc = atan2_poly(x.y, x.x) * L.w_over_2pi;
     s = 0.f;
+    r = 0.f;
     v = 0;
     for (int k = 0; k < proj_iters; ++k) {
       float sa, ca;
@@ -101,7 +106,9 @@ __device__ __forceinline__ bool project_px(const DevLevel& L, float3 x, int proj
       const float xp = fmaf(-L.r0, ca, x.x);
       const float yp = fmaf(-L.r0, sa, x.y);
       const float n2 = fmaf(xp, xp, fmaf(yp, yp, x.z * x.z));
-      s = x.z * rsqrtf(n2);
+      const float inv = rsqrtf(n2);
+      s = x.z * inv;
+      r = n2 * inv;
       v = row_from_sin(L, s);
       uc = atan2_poly(yp, xp) * L.w_over_2pi;
       if (L.has_theta) uc -= __ldg(L.thu + v);
@@ -109,6 +116,12 @@ __device__ __forceinline__ bool project_px(const DevLevel& L, float3 x, int proj
   }
   u = wrap_col(uc, L.W);
   return (s >= L.s_lo) && (s <= L.s_hi);   // false for NaN
+}
+
+template <bool R0>
+__device__ __forceinline__ bool project_px(const DevLevel& L, float3 x, int proj_iters, int& u, int& v) {
+  float r;
+  return project_px<R0>(L, x, proj_iters, u, v, r);
 }
 
 __device__ __forceinline__ bool range_ok(float r) { return r > 0.f && r < INFINITY; }

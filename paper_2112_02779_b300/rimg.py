@@ -12,7 +12,7 @@ import os
 import numpy as np
 
 from ._abi import (RIMG_MAX_LEVELS, RIMG_FLAG_DEGENERATE, RIMG_STATIC_SCRATCH_BYTES, rimg_level, rimg_sensor, rimg_params,
-                   rimg_group, rimg_adam, RIMG_CNN_IN_H, RIMG_CNN_IN_W, RIMG_CNN_MAX_BATCH,
+                   rimg_group, rimg_adam, rimg_grid, RIMG_CNN_IN_H, RIMG_CNN_IN_W, RIMG_CNN_MAX_BATCH,
                    STATUS_NAMES, HEADER_FUNCTIONS)
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -75,6 +75,8 @@ _sig("rimg_cnn_grad", _c_int, _vp, _c_int, _c_int, _c_int, _c_int, _vp, _vp, _vp
      _c_size, _vp)
 _sig("rimg_cnn_train_step", _c_int, _vp, _c_size, _c_int, _c_int, _c_int, _c_int, _vp, _vp, _vp, _vp,
      _P(rimg_adam), _c_int, _vp, _vp, _vp, _c_size, _vp)
+_sig("rimg_sdf_integrate", _c_int, _P(rimg_sensor), _c_int, _c_int, _vp, _vp, _P(rimg_grid), ctypes.c_float, _vp, _vp,
+     _P(rimg_params), _vp)
 _sig("rimg_profile_begin", _c_int, _c_int)
 _sig("rimg_profile_end", _c_int, _c_int, _P(_c_int), _P(_c_int), _P(_c_int), _P(ctypes.c_float), _P(ctypes.c_float))
 
@@ -320,6 +322,17 @@ def rimg_gemm_bf16(A, B, C, C_bf16=None, bias=None, relu=False, splits=1, err=No
                                                  _ptr(err), _stream(stream)))
 
 
+def rimg_sdf_integrate(sensor, level, range_l, T_world_to_sensor, dims, origin, voxel, sdf, weight, trunc=0.0,
+                       params=None, n_scans=None, stream=None):
+    """Projective SDF integration of n_scans level-`level` range images into
+    the dense grid (sdf, weight float32 [nz, ny, nx], updated in place)."""
+    n = range_l.shape[0] if n_scans is None else n_scans
+    g = rimg_grid(int(dims[0]), int(dims[1]), int(dims[2]), float(voxel), (ctypes.c_float * 3)(*[float(o) for o in origin]))
+    _check("rimg_sdf_integrate", _lib.rimg_sdf_integrate(
+        sensor.ref(), level, n, _ptr(range_l), _ptr(T_world_to_sensor), ctypes.byref(g), float(trunc), _ptr(sdf),
+        _ptr(weight), ctypes.byref(params) if params is not None else None, _stream(stream)))
+
+
 # ---------------------------------------------------------------------------
 # Learned pose proposal
 
@@ -443,7 +456,7 @@ def rimg_profile_end(cap=100000):
     return [(kid[i], lvl[i], npr[i], t0[i], ms[i]) for i in range(n)]
 
 
-KERNEL_NAMES = {0: "unproject", 1: "pyramid", 2: "normals", 3: "icp_step", 4: "src_pyramid", 5: "solve"}
+KERNEL_NAMES = {0: "unproject", 1: "pyramid", 2: "normals", 3: "icp_step", 4: "src_pyramid", 5: "solve", 6: "sdf"}
 
 __all__ = [n for n in dir() if n.startswith("rimg_")] + ["Sensor", "Groups", "ProposalNet", "RimgError", "KERNEL_NAMES",
                                                           "RIMG_MAX_LEVELS", "RIMG_FLAG_DEGENERATE", "lib"]

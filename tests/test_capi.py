@@ -48,17 +48,19 @@ int main(void) {
          offsetof(rimg_params, streams));
   printf("%zu %zu %zu %zu\n", sizeof(rimg_group), offsetof(rimg_group, iters), offsetof(rimg_group, params),
          offsetof(rimg_group, status));
+  printf("%zu %zu %zu\n", sizeof(rimg_grid), offsetof(rimg_grid, voxel), offsetof(rimg_grid, origin));
   return 0;
 }
 ''')
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     vals = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
-    L, S, P, G = _abi.rimg_level, _abi.rimg_sensor, _abi.rimg_params, _abi.rimg_group
+    L, S, P, G, Gr = _abi.rimg_level, _abi.rimg_sensor, _abi.rimg_params, _abi.rimg_group, _abi.rimg_grid
     assert vals == [ctypes.sizeof(L), ctypes.sizeof(S), ctypes.sizeof(P),
                     L.off_rows.offset, L.off_bins.offset, S.d_tables.offset, S.level.offset,
                     P.proj_iters.offset, P.kahan.offset, P.streams.offset,
-                    ctypes.sizeof(G), G.iters.offset, G.params.offset, G.status.offset]
+                    ctypes.sizeof(G), G.iters.offset, G.params.offset, G.status.offset,
+                    ctypes.sizeof(Gr), Gr.voxel.offset, Gr.origin.offset]
 
 
 def test_default_params_and_status_strings():
@@ -146,3 +148,28 @@ def test_cnn_entry_points_check_arguments_on_the_host():
     opt = _abi.rimg_adam(1e-3, 0.9, 0.999, 1e-8)
     assert lib.rimg_cnn_train_step(fake, 1 << 30, 4, 8, 128, 1, fake, fake, None, fake, ctypes.byref(opt), 0, None,
                                    None, fake, 1 << 40, None) == -1
+
+
+def test_sdf_entry_point_checks_arguments_on_the_host():
+    lib = R.lib()
+    phi = np.deg2rad(np.linspace(10, -20, 16))
+    s = _abi.rimg_sensor()
+    # a sensor struct built against a fake device pointer (host checks only)
+    assert R.lib().rimg_sensor_build(16, 64, 2, phi.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                     np.zeros(16).ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 0.0, 4096, 16,
+                                     ctypes.byref(s)) == -4
+    g = _abi.rimg_grid(4, 4, 4, 0.1, (ctypes.c_float * 3)(0, 0, 0))
+    fake = 1 << 20
+    assert lib.rimg_sdf_integrate(None, 0, 1, fake, fake, ctypes.byref(g), 0.0, fake, fake, None, None) == -1
+    bad = _abi.rimg_grid(4, 4, 4, 0.0, (ctypes.c_float * 3)(0, 0, 0))
+    s.d_tables = fake
+    s.H, s.W, s.levels = 16, 64, 1
+    s.level[0].H, s.level[0].W = 16, 64
+    assert lib.rimg_sdf_integrate(ctypes.byref(s), 0, 1, fake, fake, ctypes.byref(bad), 0.0, fake, fake, None,
+                                  None) == -1                       # voxel size <= 0
+    assert lib.rimg_sdf_integrate(ctypes.byref(s), 1, 1, fake, fake, ctypes.byref(g), 0.0, fake, fake, None,
+                                  None) == -1                       # level out of range
+    assert lib.rimg_sdf_integrate(ctypes.byref(s), 0, 1, None, fake, ctypes.byref(g), 0.0, fake, fake, None,
+                                  None) == -1                       # missing images
+    assert lib.rimg_sdf_integrate(ctypes.byref(s), 0, 0, None, None, ctypes.byref(g), 0.0, None, None, None,
+                                  None) == 0                        # no scans: no-op
