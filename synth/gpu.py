@@ -207,3 +207,45 @@ def make_pairs_gpu(cfg, indices, noise=True, device="cuda", processes=1, drawn=N
         if tmp is not out:
             out[:, c0:c1] = tmp
     return out[1], out[0], T
+
+
+def make_sequence_gpu(cfg, n_scans, seed, step=1.0, device="cuda"):
+    """n_scans scans of ONE outdoor scene of `cfg` (objects drawn as in
+    draw_pair, clear of every sensor position), the sensor 1.7 m above the
+    ground moving `step` m along x per scan with a slow yaw drift (0.02 rad
+    per scan).  Returns (ranges [n, H, W] float32 on the device, world poses
+    [n, 4, 4] float64: sensor -> world)."""
+    import torch
+    lib = _load()
+    sensor = cfg.sensor()
+    rng = np.random.default_rng(np.random.SeedSequence([cfg.config_id, seed, 11]))
+    poses = np.zeros((n_scans, 4, 4))
+    for k in range(n_scans):
+        yaw = 0.02 * k
+        poses[k] = np.eye(4)
+        poses[k, :3, :3] = [[np.cos(yaw), -np.sin(yaw), 0], [np.sin(yaw), np.cos(yaw), 0], [0, 0, 1]]
+        poses[k, :3, 3] = [step * (k - 0.5 * (n_scans - 1)), 0.0, 1.7]
+    obj = outdoor_objects(rng, cfg.n_objects, cfg.r_max, keep=poses[:, :2, 3]).astype(np.float32)
+    n_pairs = (n_scans + 1) // 2
+    objs = np.broadcast_to(obj, (n_pairs,) + obj.shape).copy()
+    P = np.zeros((n_pairs, 2, 12))
+    for k in range(2 * n_pairs):
+        W = poses[min(k, n_scans - 1)]
+        P[k // 2, k % 2, :9] = W[:3, :3].ravel()
+        P[k // 2, k % 2, 9:] = W[:3, 3]
+    seeds = np.array([pair_seed(cfg, 10 ** 6 + seed * 4096 + p) for p in range(n_pairs)], np.uint64)
+    out = torch.empty((2, n_pairs, cfg.H, cfg.W), dtype=torch.float32, device=device)
+    rows = torch.from_numpy(sensor_rows(sensor)).to(device)
+    d_objs = torch.from_numpy(objs).to(device)
+    d_nobj = torch.full((n_pairs,), obj.shape[0], dtype=torch.int32, device=device)
+    d_poses = torch.from_numpy(P).to(device)
+    d_seed = torch.from_numpy(seeds.view(np.int64)).to(device)
+    rc = lib.synth_raycast(n_pairs, cfg.H, cfg.W, rows.data_ptr(), float(sensor.r0), d_objs.data_ptr(),
+                           d_nobj.data_ptr(), obj.shape[0], d_poses.data_ptr(), float(cfg.r_min), float(cfg.r_max),
+                           float(cfg.sigma), float(cfg.dropout), d_seed.data_ptr(), out.data_ptr(),
+                           torch.cuda.current_stream().cuda_stream)
+    if rc != 0:
+        raise RuntimeError(f"synth_raycast failed ({rc})")
+    # scan 2p + k is out[k, p]
+    scans = out.permute(1, 0, 2, 3).reshape(2 * n_pairs, cfg.H, cfg.W)[:n_scans].contiguous()
+    return scans, poses
