@@ -460,3 +460,33 @@ def pose_error(T, T_ref):
     R, Rr = np.asarray(T)[:3, :3], np.asarray(T_ref)[:3, :3]
     c = np.clip((np.trace(R @ Rr.T) - 1.0) / 2.0, -1.0, 1.0)
     return float(np.arccos(c)), float(np.linalg.norm(np.asarray(T)[:3, 3] - np.asarray(T_ref)[:3, 3]))
+
+
+# ----------------------------------------------------------------------------
+# Point clouds without scan structure (Section 3.2, last paragraph): projected
+# into a range image through Pi; each pixel keeps its nearest point.
+
+def points_to_range(X, phi_lut, theta_lut, r0, W):
+    """Range image [H, W] of points X (n, 3) (already in the sensor frame):
+    pixel (u, v) = Pi(x) holds the smallest range r of the points projecting
+    there inside the vertical field of view; pixels without points hold +inf.
+    Also returns a mask of pixels that a near-tie point (within NEAR_TIE_PX
+    of a column boundary or NEAR_TIE_ROW of a row boundary) could have
+    reached: the pixel it was given and its 8 neighbours (columns wrap)."""
+    X = np.asarray(X, np.float64).reshape(-1, 3)
+    H = len(phi_lut)
+    ok = np.all(np.isfinite(X), axis=1)
+    Xs = np.where(ok[:, None], X, 1.0)
+    u, v, r, fov, det = project(Xs, phi_lut, theta_lut, r0, W, return_detail=True)
+    keep = ok & fov & (r > 0)
+    img = np.full((H, W), np.inf)
+    np.minimum.at(img, (v[keep], u[keep]), r[keep])
+    m_u = np.abs(np.mod(det["u_c"], 1.0) - 0.5)
+    m_v = row_margin(np.where(np.isfinite(det["phi"]), det["phi"], 0.0), phi_lut)
+    near_pt = ok & ((m_u < NEAR_TIE_PX) | (m_v < NEAR_TIE_ROW)) & (r > 0)
+    near = np.zeros((H, W), bool)
+    for dv in (-1, 0, 1):
+        for du in (-1, 0, 1):
+            vv = np.clip(v[near_pt] + dv, 0, H - 1)
+            near[vv, np.mod(u[near_pt] + du, W)] = True
+    return img, near
