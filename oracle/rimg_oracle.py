@@ -269,6 +269,69 @@ def normals(range_img, phi_lut, theta_lut, r0, rel_jump, return_margin=False):
     return n, ok
 
 
+PCA_MIN_POINTS = 5          # points of the 3x3 window needed for a PCA normal
+PCA_COLLINEAR = 1e-4        # lambda_1 <= this * lambda_2: the window's points lie on a line
+
+
+def normals_pca(range_img, phi_lut, theta_lut, r0, rel_jump, return_detail=False):
+    """Normal image by eigen-decomposition of the 3x3 pixel window (the
+    alternative Section 4.1 names beside the cross product).
+
+    The window of pixel (u, v) holds the valid points of rows v-1 .. v+1 and
+    columns u-1 .. u+1 (u wraps) whose range differs from the centre's by at
+    most rel_jump times the centre's range.  With k >= PCA_MIN_POINTS such
+    points (the centre included), the normal is the eigenvector of the
+    smallest eigenvalue of their scatter matrix sum (p - mean)(p - mean)^T,
+    oriented so that n . P <= 0 (P the centre point); the plane offset of the
+    library's plane image is then n . P.  Invalid on rows 0 and H-1, at an
+    invalid centre, with fewer points, or when lambda_1 <= PCA_COLLINEAR *
+    lambda_2 (collinear points leave the normal undetermined).
+
+    Returns n (H, W, 3) (zero where invalid) and the validity mask; with
+    return_detail also the eigenvalues (H, W, 3) ascending, the point count
+    and the relative distance of the collinearity test to its threshold."""
+    rimg = np.asarray(range_img, np.float64)
+    H, W = rimg.shape
+    P, valid = unproject(rimg, phi_lut, theta_lut, r0)
+    r = np.where(valid, rimg, 0.0)
+    pts = np.zeros((H, W, 9, 3))
+    use = np.zeros((H, W, 9), bool)
+    k = 0
+    for dv in (-1, 0, 1):
+        for du in (-1, 0, 1):
+            Pn = np.zeros_like(P)
+            rn = np.zeros_like(r)
+            vn = np.zeros_like(valid)
+            src_rows = slice(max(0, dv), H + min(0, dv))
+            dst_rows = slice(max(0, -dv), H + min(0, -dv))
+            Pn[dst_rows] = np.roll(P, -du, axis=1)[src_rows]
+            rn[dst_rows] = np.roll(r, -du, axis=1)[src_rows]
+            vn[dst_rows] = np.roll(valid, -du, axis=1)[src_rows]
+            pts[:, :, k] = Pn
+            use[:, :, k] = vn & valid & (np.abs(rn - r) <= rel_jump * r)
+            k += 1
+    cnt = use.sum(axis=-1)
+    w = use[..., None].astype(np.float64)
+    mean = (pts * w).sum(axis=2) / np.maximum(cnt, 1)[..., None]
+    q = (pts - mean[:, :, None, :]) * w
+    C = np.einsum("hwki,hwkj->hwij", q, q)
+    lam, vec = np.linalg.eigh(C.reshape(-1, 3, 3))
+    lam = lam.reshape(H, W, 3)
+    n = vec[:, :, 0].reshape(H, W, 3)
+    rows = np.zeros((H, 1), bool)
+    rows[1:H - 1] = True
+    thr = PCA_COLLINEAR * lam[..., 2]
+    ok = valid & rows & (cnt >= PCA_MIN_POINTS) & (lam[..., 1] > thr)
+    flip = np.sum(n * P, axis=-1) > 0
+    n = np.where(flip[..., None], -n, n)
+    n = np.where(ok[..., None], n, 0.0)
+    if return_detail:
+        with np.errstate(invalid="ignore", divide="ignore"):
+            margin = np.where(thr > 0, np.abs(lam[..., 1] - thr) / thr, np.inf)
+        return n, ok, dict(lam=lam, count=cnt, margin=margin)
+    return n, ok
+
+
 # ----------------------------------------------------------------------------
 # Section 4.1: projective association (Eq. 5-6), point-to-plane loss and
 # the Gauss-Newton normal equations of Eq. 7
