@@ -93,6 +93,8 @@ typedef struct rimg_params {
   int proj_iters;           /* receiver-offset fixed-point steps when r0 != 0 (1..16) */
   int kahan;                /* 1: Kahan-compensated FP32 accumulation of J^T W J / J^T W e */
   int streams;              /* rimg_register: concurrent sub-batches (internal streams), 1..4 */
+  int normal_method;        /* 0: cross product of neighbour pixels (default); 1: PCA of the 3x3
+                               window -- Section 4.1 names both (see rimg_normals) */
 } rimg_params;
 
 /* Fill *p with the defaults above.  Host only. */
@@ -161,6 +163,12 @@ int rimg_pyramid(int n_images, int H, int W, int levels, int channels, const flo
  * Invalid (plane = 0) on rows 0 and H-1, when any of the five ranges is invalid,
  * when |r_nb - r_c| > normal_rel_jump * r_c for a neighbour (decided exactly),
  * or when |a x b| <= 1e-4 |a| |b|.
+ * With p->normal_method = 1 (PCA, the eigen-decomposition alternative of
+ * Section 4.1): the 3x3 window's points whose range passes the same jump test
+ * (at least 5 of the nine, the centre included) give the scatter matrix
+ * sum (p - mean)(p - mean)^T; n is the eigenvector of its smallest eigenvalue,
+ * flipped as above; invalid on rows 0 and H-1, at an invalid centre, with
+ * fewer points, or when lambda_1 <= 1e-4 lambda_2 (collinear points).
  * Output is a plane image per level: planes_levels (HOST array of s->levels
  * device pointers) entry l receives float4 [n][H_l][W_l] = (n_x, n_y, n_z, d)
  * with d = n . P, strided from the finest level like rimg_pyramid (normals are
@@ -349,6 +357,27 @@ int rimg_register_host_async(const rimg_sensor* src, const rimg_sensor* dst, int
                              size_t workspace_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Point clouds without scan structure (Section 3.2, last paragraph: clouds
+ * such as KITTI's enter the same path through a synthetic sensor, theta_lut
+ * = 0 and rows evenly spread over the field of view -- any rimg_sensor works).
+ * Each point x (optionally moved by T_cloud_to_sensor, float64 [n][16]
+ * device, nullable = identity) is projected by Pi at pyramid level `level`;
+ * pixel (u, v) keeps the smallest range r = |x - o| of the points that land on
+ * it inside the vertical field of view (an exact, order-independent minimum).
+ * Pixels without a point are set to +inf, which is an invalid range for every
+ * entry point of this library.
+ *
+ * xyz: float32 [n_clouds][max_points][3] device; counts (nullable): int32
+ * [n_clouds] device, points used per cloud (NULL: all max_points); points
+ * with a non-finite coordinate are skipped.  range_l: float32
+ * [n_clouds][H_l][W_l] device, overwritten.  p (nullable): only proj_iters is
+ * used.  n_clouds <= 65535.
+ * ------------------------------------------------------------------------- */
+int rimg_points_to_range(const rimg_sensor* sensor, int level, int n_clouds, int max_points, const float* xyz,
+                         const int* counts, const double* T_cloud_to_sensor, float* range_l, const rimg_params* p,
+                         void* stream);
+
+/* ---------------------------------------------------------------------------
  * Projective SDF integration, Section 4.2 (Eq. 8-10), on a dense voxel grid.
  *
  * For each voxel centre x = origin + voxel * (i + 1/2, j + 1/2, k + 1/2) and
@@ -487,7 +516,8 @@ int rimg_cnn_train_step(void* state, size_t state_bytes, int n, int H, int W, in
  * caller take the union of intervals.
  * Kernel ids: 0 unproject, 1 pyramid, 2 normals (+ plane pyramid),
  * 3 icp step (association + reduction), 4 source-range pyramid, 5 FP64
- * solve + pose update, 6 SDF integration.  Not for use during stream capture.
+ * solve + pose update, 6 SDF integration, 7 point-cloud projection.  Not for
+ * use during stream capture.
  * ------------------------------------------------------------------------- */
 int rimg_profile_begin(int max_launches);
 int rimg_profile_end(int cap, int* kernel_id, int* level, int* n_pairs, float* start_ms, float* ms);

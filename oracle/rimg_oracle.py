@@ -460,9 +460,13 @@ class Target:
     """A target scan prepared for association: range pyramid plus strided
     normal images (Section 4.1)."""
 
-    def __init__(self, dst_range, phi_lut, theta_lut, r0, levels, rel_jump):
+    def __init__(self, dst_range, phi_lut, theta_lut, r0, levels, rel_jump, normal_method="cross"):
         self.phi, self.theta, self.r0 = np.asarray(phi_lut, np.float64), np.asarray(theta_lut, np.float64), float(r0)
-        n0, ok0, m0 = normals(dst_range, self.phi, self.theta, self.r0, rel_jump, return_margin=True)
+        if normal_method == "pca":
+            n0, ok0, det = normals_pca(dst_range, self.phi, self.theta, self.r0, rel_jump, return_detail=True)
+            m0 = det["margin"]
+        else:
+            n0, ok0, m0 = normals(dst_range, self.phi, self.theta, self.r0, rel_jump, return_margin=True)
         self.range = pyramid(np.asarray(dst_range), levels)
         self.n = pyramid(n0, levels)
         self.nvalid = pyramid(ok0, levels)
@@ -499,7 +503,8 @@ def register(src_range, dst_range, src_sensor, dst_sensor, T_init, levels, iters
     (phi_lut, theta_lut, r0) tuples."""
     assert len(iters) == levels
     sp, st, sr0 = src_sensor
-    target = Target(dst_range, *dst_sensor, levels, params.get("normal_rel_jump", np.float32(0.1)))
+    target = Target(dst_range, *dst_sensor, levels, params.get("normal_rel_jump", np.float32(0.1)),
+                    params.get("normal_method", "cross"))
     T = np.array(T_init, np.float64)
     degenerate = False
     hist = []

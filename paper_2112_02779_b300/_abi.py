@@ -27,7 +27,7 @@ class rimg_sensor(ctypes.Structure):
 class rimg_params(ctypes.Structure):
     _fields_ = [("huber_delta", ctypes.c_float), ("max_corr_dist", ctypes.c_float),
                 ("normal_rel_jump", ctypes.c_float), ("proj_iters", ctypes.c_int), ("kahan", ctypes.c_int),
-                ("streams", ctypes.c_int)]
+                ("streams", ctypes.c_int), ("normal_method", ctypes.c_int)]
 
 
 class rimg_group(ctypes.Structure):
@@ -47,7 +47,7 @@ HEADER_FUNCTIONS = [
     "rimg_register_workspace_bytes", "rimg_register", "rimg_register_last_sums",
     "rimg_register_groups_workspace_bytes", "rimg_register_groups", "rimg_autotune", "rimg_autotune_clear",
     "rimg_register_host_workspace_bytes", "rimg_register_host", "rimg_register_host_async",
-    "rimg_gemm_bf16", "rimg_profile_begin", "rimg_profile_end", "rimg_sdf_integrate",
+    "rimg_gemm_bf16", "rimg_profile_begin", "rimg_profile_end", "rimg_sdf_integrate", "rimg_points_to_range",
     "rimg_cnn_param_count", "rimg_cnn_state_bytes", "rimg_cnn_workspace_bytes", "rimg_cnn_init", "rimg_cnn_load",
     "rimg_propose", "rimg_cnn_grad", "rimg_cnn_train_step",
 ]

@@ -103,6 +103,93 @@ struct PlaneOut {
   float4* p[RIMG_MAX_LEVELS];
 };
 
+// The PCA variant (the eigen-decomposition alternative of Section 4.1): the
+// window's points whose range passes the same jump test as the cross
+// product's neighbours (at least kPcaMinPoints of the nine, centre included)
+// give the scatter matrix C = sum (p - mean)(p - mean)^T; its eigenvalues come
+// from the closed form for symmetric 3x3 matrices (trace / deviation /
+// determinant, one acos and two cos), the normal from the largest cross
+// product of two rows of C - lambda_0 I.  Invalid when lambda_1 <= 1e-4
+// lambda_2 (collinear points).
+// Plane (n, n . P) of pixel (u, v) to level 0 and, when its coordinates are
+// multiples of 2^l, to level l; the optional mask gets the validity.
+__device__ __forceinline__ void write_plane(const PlaneOut& out, uint8_t* mask0, int img, int H, int W, int u, int v,
+                                            int levels, float4 plane, bool ok) {
+  const long long N = (long long)H * W;
+  out.p[0][img * N + (long long)v * W + u] = plane;
+  if (mask0) mask0[img * N + (long long)v * W + u] = ok ? 1 : 0;
+  // unrolled so the level pointers are read with constant indices (no local copy)
+#pragma unroll
+  for (int l = 1; l < RIMG_MAX_LEVELS; ++l) {
+    const int m = (1 << l) - 1;
+    if (l >= levels || ((u & m) | (v & m))) break;
+    const int Hl = H >> l, Wl = W >> l;
+    out.p[l][img * (long long)Hl * Wl + (long long)(v >> l) * Wl + (u >> l)] = plane;
+  }
+}
+
+constexpr int kPcaMinPoints = 5;
+constexpr float kPcaCollinear = 1e-4f;
+
+__device__ __forceinline__ bool pca_normal(const float (&q)[9][3], const bool (&use)[9], float& nx, float& ny,
+                                           float& nz) {
+  float k = 0.f, mx = 0.f, my = 0.f, mz = 0.f;
+#pragma unroll
+  for (int i = 0; i < 9; ++i)
+    if (use[i]) { k += 1.f; mx += q[i][0]; my += q[i][1]; mz += q[i][2]; }
+  if (k < (float)kPcaMinPoints) return false;
+  const float ik = 1.f / k;
+  mx *= ik; my *= ik; mz *= ik;
+  float c00 = 0.f, c01 = 0.f, c02 = 0.f, c11 = 0.f, c12 = 0.f, c22 = 0.f;
+#pragma unroll
+  for (int i = 0; i < 9; ++i)
+    if (use[i]) {
+      const float a = q[i][0] - mx, b = q[i][1] - my, c = q[i][2] - mz;
+      c00 = fmaf(a, a, c00); c01 = fmaf(a, b, c01); c02 = fmaf(a, c, c02);
+      c11 = fmaf(b, b, c11); c12 = fmaf(b, c, c12); c22 = fmaf(c, c, c22);
+    }
+  // scale to O(1) (the eigenvectors do not change)
+  const float sc = fmaxf(fmaxf(fmaxf(fabsf(c00), fabsf(c11)), fmaxf(fabsf(c22), fabsf(c01))),
+                         fmaxf(fabsf(c02), fabsf(c12)));
+  if (!(sc > 0.f)) return false;
+  const float is = 1.f / sc;
+  c00 *= is; c01 *= is; c02 *= is; c11 *= is; c12 *= is; c22 *= is;
+  const float qm = (c00 + c11 + c22) * (1.f / 3.f);
+  const float b00 = c00 - qm, b11 = c11 - qm, b22 = c22 - qm;
+  const float off = fmaf(c01, c01, fmaf(c02, c02, c12 * c12));
+  const float p2 = fmaf(b00, b00, fmaf(b11, b11, fmaf(b22, b22, 2.f * off))) * (1.f / 6.f);
+  if (!(p2 > 0.f)) return false;                     // isotropic: no preferred direction
+  const float p = sqrtf(p2), ip = 1.f / p;
+  // det((C - q I) / p) / 2
+  const float d00 = b00 * ip, d11 = b11 * ip, d22 = b22 * ip, e01 = c01 * ip, e02 = c02 * ip, e12 = c12 * ip;
+  const float det = d00 * fmaf(d11, d22, -e12 * e12) - e01 * fmaf(e01, d22, -e12 * e02) +
+                    e02 * fmaf(e01, e12, -d11 * e02);
+  const float hr = fminf(1.f, fmaxf(-1.f, 0.5f * det));
+  const float phi = acosf(hr) * (1.f / 3.f);
+  const float l2 = fmaf(2.f * p, cosf(phi), qm);
+  const float l0 = fmaf(2.f * p, cosf(phi + 2.0943951023931953f), qm);
+  const float l1 = 3.f * qm - l0 - l2;
+  if (!(l1 > kPcaCollinear * l2)) return false;
+  // null vector of C - l0 I: the longest cross product of two of its rows
+  const float r0x = c00 - l0, r0y = c01, r0z = c02;
+  const float r1x = c01, r1y = c11 - l0, r1z = c12;
+  const float r2x = c02, r2y = c12, r2z = c22 - l0;
+  const float ax = fmaf(r0y, r1z, -r0z * r1y), ay = fmaf(r0z, r1x, -r0x * r1z), az = fmaf(r0x, r1y, -r0y * r1x);
+  const float bx = fmaf(r0y, r2z, -r0z * r2y), by = fmaf(r0z, r2x, -r0x * r2z), bz = fmaf(r0x, r2y, -r0y * r2x);
+  const float cx = fmaf(r1y, r2z, -r1z * r2y), cy = fmaf(r1z, r2x, -r1x * r2z), cz = fmaf(r1x, r2y, -r1y * r2x);
+  const float na = fmaf(ax, ax, fmaf(ay, ay, az * az));
+  const float nb = fmaf(bx, bx, fmaf(by, by, bz * bz));
+  const float nc = fmaf(cx, cx, fmaf(cy, cy, cz * cz));
+  float vx = ax, vy = ay, vz = az, vn = na;
+  if (nb > vn) { vx = bx; vy = by; vz = bz; vn = nb; }
+  if (nc > vn) { vx = cx; vy = cy; vz = cz; vn = nc; }
+  if (!(vn > 0.f)) return false;
+  const float inv = rsqrtf(vn);
+  nx = vx * inv; ny = vy * inv; nz = vz * inv;
+  return true;
+}
+
+template <bool PCA>
 __global__ void __launch_bounds__(NT_X* NT_Y) k_normals(DevLevel L, int levels, int n, const float* __restrict__ range,
                                                         float rel_jump, PlaneOut out,
                                                         uint8_t* __restrict__ mask0) {
@@ -133,6 +220,30 @@ __global__ void __launch_bounds__(NT_X* NT_Y) k_normals(DevLevel L, int levels, 
   if (u >= W || v >= H) return;
   const int cx = threadIdx.x + 1, cy = threadIdx.y + 1;
   const float rc = sr[cy][cx];
+  if (PCA) {
+    float q[9][3];
+    bool use[9];
+    const float px = sx[cy][cx], py = sy[cy][cx], pz = sz[cy][cx];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const int yy = cy + i / 3 - 1, xx = cx + i % 3 - 1;
+      const float rn = sr[yy][xx];
+      use[i] = rc > 0.f && rn > 0.f && fmaf(rel_jump, rc, -fabsf(rn - rc)) >= 0.f;
+      q[i][0] = sx[yy][xx] - px;
+      q[i][1] = sy[yy][xx] - py;
+      q[i][2] = sz[yy][xx] - pz;
+    }
+    float nx = 0.f, ny = 0.f, nz = 0.f;
+    bool ok = (v > 0) && (v < H - 1) && rc > 0.f && pca_normal(q, use, nx, ny, nz);
+    float4 plane = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (ok) {
+      float d = fmaf(nx, px, fmaf(ny, py, nz * pz));
+      if (d > 0.f) { nx = -nx; ny = -ny; nz = -nz; d = -d; }
+      plane = make_float4(nx, ny, nz, d);
+    }
+    write_plane(out, mask0, img, H, W, u, v, levels, plane, ok);
+    return;
+  }
   const float rl = sr[cy][cx - 1], rr = sr[cy][cx + 1], ru = sr[cy - 1][cx], rd = sr[cy + 1][cx];
   // |r_nb - r_c| <= rel_jump * r_c decided exactly: the difference is exact
   // (Sterbenz) whenever the test can pass, and the sign of one fused
@@ -158,20 +269,10 @@ __global__ void __launch_bounds__(NT_X* NT_Y) k_normals(DevLevel L, int levels, 
     if (d > 0.f) { nx = -nx; ny = -ny; nz = -nz; d = -d; }
     plane = make_float4(nx, ny, nz, d);
   }
-  const long long N = (long long)H * W;
-  out.p[0][img * N + (long long)v * W + u] = plane;
-  if (mask0) mask0[img * N + (long long)v * W + u] = ok ? 1 : 0;
-  // unrolled so the level pointers are read with constant indices (no local copy)
-#pragma unroll
-  for (int l = 1; l < RIMG_MAX_LEVELS; ++l) {
-    const int m = (1 << l) - 1;
-    if (l >= levels || ((u & m) | (v & m))) break;
-    const int Hl = H >> l, Wl = W >> l;
-    out.p[l][img * (long long)Hl * Wl + (long long)(v >> l) * Wl + (u >> l)] = plane;
-  }
+  write_plane(out, mask0, img, H, W, u, v, levels, plane, ok);
 }
 
-cudaError_t launch_normals(const rimg_sensor* s, int n, const float* range, float rel_jump,
+cudaError_t launch_normals(const rimg_sensor* s, int n, const float* range, float rel_jump, int method,
                            float* const* planes_levels, uint8_t* mask0, cudaStream_t st) {
   const DevLevel L = dev_level(s, 0);
   const long long N = (long long)L.H * L.W;
@@ -181,8 +282,12 @@ cudaError_t launch_normals(const rimg_sensor* s, int n, const float* range, floa
     for (int l = 0; l < s->levels; ++l)
       o.p[l] = reinterpret_cast<float4*>(planes_levels[l]) + (long long)off * (L.H >> l) * (L.W >> l);
     dim3 grid((L.W + NT_X - 1) / NT_X, (L.H + NT_Y - 1) / NT_Y, cnt);
-    k_normals<<<grid, dim3(NT_X, NT_Y), 0, st>>>(L, s->levels, cnt, range + off * N, rel_jump, o,
-                                                 mask0 ? mask0 + off * N : nullptr);
+    if (method == 1)
+      k_normals<true><<<grid, dim3(NT_X, NT_Y), 0, st>>>(L, s->levels, cnt, range + off * N, rel_jump, o,
+                                                         mask0 ? mask0 + off * N : nullptr);
+    else
+      k_normals<false><<<grid, dim3(NT_X, NT_Y), 0, st>>>(L, s->levels, cnt, range + off * N, rel_jump, o,
+                                                          mask0 ? mask0 + off * N : nullptr);
   }
   return cudaGetLastError();
 }

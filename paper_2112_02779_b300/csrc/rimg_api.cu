@@ -78,6 +78,7 @@ int check_params(const rimg_params* p) {
   if (!(p->normal_rel_jump >= 0.f && p->normal_rel_jump < 0.5f)) return RIMG_ERR_INVALID_ARG;
   if (p->proj_iters < 1 || p->proj_iters > 16) return RIMG_ERR_INVALID_ARG;
   if (p->streams < 1 || p->streams > 4) return RIMG_ERR_INVALID_ARG;
+  if (p->normal_method != 0 && p->normal_method != 1) return RIMG_ERR_INVALID_ARG;
   return RIMG_OK;
 }
 
@@ -272,7 +273,7 @@ int prep_slice(const rimg_sensor* src, const rimg_sensor* dst, int n, const floa
   rimg_sensor dview = *dst;
   dview.levels = levels;
   prof_before(st, K_NORMALS, 0, n);
-  cudaError_t e = launch_normals(&dview, n, dst_range, p->normal_rel_jump, planes, nullptr, st);
+  cudaError_t e = launch_normals(&dview, n, dst_range, p->normal_rel_jump, p->normal_method, planes, nullptr, st);
   prof_after(st);
   if (e != cudaSuccess) return cuda_fail(e, "normals kernel");
   if (levels > 1) {
@@ -488,6 +489,7 @@ int rimg_default_params(rimg_params* p) {
   p->proj_iters = 3;
   p->kahan = 1;
   p->streams = 2;
+  p->normal_method = 0;
   return RIMG_OK;
 }
 
@@ -673,6 +675,27 @@ int rimg_sdf_integrate(const rimg_sensor* s, int level, int n_scans, const float
   return RIMG_OK;
 }
 
+int rimg_points_to_range(const rimg_sensor* s, int level, int n_clouds, int max_points, const float* xyz,
+                         const int* counts, const double* T_cloud_to_sensor, float* range_l, const rimg_params* p,
+                         void* stream) {
+  int rc = check_sensor(s);
+  if (rc) return rc;
+  if (level < 0 || level >= s->levels || n_clouds < 0 || n_clouds > 65535 || max_points < 0)
+    return RIMG_ERR_INVALID_ARG;
+  if (p && (rc = check_params(p))) return rc;
+  if (n_clouds == 0) return RIMG_OK;
+  if (!range_l || (max_points > 0 && !xyz)) return RIMG_ERR_INVALID_ARG;
+  rimg_params d;
+  rimg_default_params(&d);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  prof_before(st, K_POINTS, level, n_clouds);
+  cudaError_t e = launch_points(dev_level(s, level), n_clouds, max_points, xyz, counts, T_cloud_to_sensor,
+                                p ? p->proj_iters : d.proj_iters, range_l, st);
+  prof_after(st);
+  if (e != cudaSuccess) return cuda_fail(e, "points kernel");
+  return RIMG_OK;
+}
+
 int rimg_pyramid(int n_images, int H, int W, int levels, int channels, const float* in,
                  float* const* out_levels, void* stream) {
   if (n_images < 0 || H <= 0 || W <= 0 || levels < 1 || levels > RIMG_MAX_LEVELS) return RIMG_ERR_INVALID_ARG;
@@ -707,7 +730,7 @@ int rimg_normals(const rimg_sensor* s, int n_images, const float* range, const r
     if (!planes_levels[l]) return RIMG_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   prof_before(st, K_NORMALS, 0, n_images);
-  cudaError_t e = launch_normals(s, n_images, range, p->normal_rel_jump, planes_levels, mask0, st);
+  cudaError_t e = launch_normals(s, n_images, range, p->normal_rel_jump, p->normal_method, planes_levels, mask0, st);
   prof_after(st);
   if (e != cudaSuccess) return cuda_fail(e, "normals kernel");
   return RIMG_OK;

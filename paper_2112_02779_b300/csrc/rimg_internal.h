@@ -23,7 +23,7 @@ struct DevLevel {
 
 DevLevel dev_level(const rimg_sensor* s, int level);
 
-enum KernelId { K_UNPROJECT = 0, K_PYRAMID = 1, K_NORMALS = 2, K_ICP = 3, K_SRC_PYRAMID = 4, K_SOLVE = 5, K_SDF = 6 };
+enum KernelId { K_UNPROJECT = 0, K_PYRAMID = 1, K_NORMALS = 2, K_ICP = 3, K_SRC_PYRAMID = 4, K_SOLVE = 5, K_SDF = 6, K_POINTS = 7 };
 
 // Launch-timing hooks (no-ops unless rimg_profile_begin was called).
 void prof_before(cudaStream_t st, int kernel, int level, int n);
@@ -34,7 +34,7 @@ cudaError_t launch_unproject(const DevLevel& L, int n, const float* range, float
                              uint8_t* mask, cudaStream_t st);
 cudaError_t launch_pyramid(int n, int H, int W, int levels, int channels, const float* in,
                            float* const* out_levels, cudaStream_t st);
-cudaError_t launch_normals(const rimg_sensor* s, int n, const float* range, float rel_jump,
+cudaError_t launch_normals(const rimg_sensor* s, int n, const float* range, float rel_jump, int method,
                            float* const* planes_levels, uint8_t* mask0, cudaStream_t st);
 
 struct IcpLaunch {
@@ -67,6 +67,9 @@ cudaError_t launch_solve(int n_pairs, double* sums, double* pose, int* status, c
 cudaError_t launch_sdf(const DevLevel& L, int n_scans, const float* ranges, const double* poses, int nx, int ny,
                        int nz, float ox, float oy, float oz, float voxel, float trunc, int proj_iters, float* sdf,
                        float* weight, cudaStream_t st);
+
+cudaError_t launch_points(const DevLevel& L, int n_clouds, int max_points, const float* xyz, const int* counts,
+                          const double* T, int proj_iters, float* img, cudaStream_t st);
 
 cudaError_t launch_gemm_bf16(int M, int N, int K, const void* A, int lda, const void* B, int ldb, float* C, int ldc,
                              void* Cbf, const float* bias, int relu, int splits, int* err, cudaStream_t st);

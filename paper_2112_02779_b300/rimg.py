@@ -77,6 +77,7 @@ _sig("rimg_cnn_train_step", _c_int, _vp, _c_size, _c_int, _c_int, _c_int, _c_int
      _P(rimg_adam), _c_int, _vp, _vp, _vp, _c_size, _vp)
 _sig("rimg_sdf_integrate", _c_int, _P(rimg_sensor), _c_int, _c_int, _vp, _vp, _P(rimg_grid), ctypes.c_float, _vp, _vp,
      _P(rimg_params), _vp)
+_sig("rimg_points_to_range", _c_int, _P(rimg_sensor), _c_int, _c_int, _c_int, _vp, _vp, _vp, _vp, _P(rimg_params), _vp)
 _sig("rimg_profile_begin", _c_int, _c_int)
 _sig("rimg_profile_end", _c_int, _c_int, _P(_c_int), _P(_c_int), _P(_c_int), _P(ctypes.c_float), _P(ctypes.c_float))
 
@@ -333,6 +334,15 @@ def rimg_sdf_integrate(sensor, level, range_l, T_world_to_sensor, dims, origin, 
         _ptr(weight), ctypes.byref(params) if params is not None else None, _stream(stream)))
 
 
+def rimg_points_to_range(sensor, level, xyz, range_l, counts=None, T_cloud_to_sensor=None, params=None, stream=None):
+    """Range images [n, H_l, W_l] of point clouds xyz float32 [n, max_points, 3]
+    (nearest point per pixel, +inf where no point lands)."""
+    n, m = xyz.shape[0], xyz.shape[1]
+    _check("rimg_points_to_range", _lib.rimg_points_to_range(
+        sensor.ref(), level, n, m, _ptr(xyz), _ptr(counts), _ptr(T_cloud_to_sensor), _ptr(range_l),
+        ctypes.byref(params) if params is not None else None, _stream(stream)))
+
+
 # ---------------------------------------------------------------------------
 # Learned pose proposal
 
@@ -456,7 +466,7 @@ def rimg_profile_end(cap=100000):
     return [(kid[i], lvl[i], npr[i], t0[i], ms[i]) for i in range(n)]
 
 
-KERNEL_NAMES = {0: "unproject", 1: "pyramid", 2: "normals", 3: "icp_step", 4: "src_pyramid", 5: "solve", 6: "sdf"}
+KERNEL_NAMES = {0: "unproject", 1: "pyramid", 2: "normals", 3: "icp_step", 4: "src_pyramid", 5: "solve", 6: "sdf", 7: "points"}
 
 __all__ = [n for n in dir() if n.startswith("rimg_")] + ["Sensor", "Groups", "ProposalNet", "RimgError", "KERNEL_NAMES",
                                                           "RIMG_MAX_LEVELS", "RIMG_FLAG_DEGENERATE", "lib"]
