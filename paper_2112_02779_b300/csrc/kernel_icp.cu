@@ -1,9 +1,12 @@
 // The fused projective-association Gauss-Newton step (Section 4.1, Eq. 5-7):
 // per source pixel unproject -> transform -> project -> gather the target
-// plane -> residual, pseudo-Huber weight, Jacobian -> 29 reduced terms; warp
-// shuffle, block and one-pass grid reduction (last-block-done counter, no
-// spinning); the last block of each pair reduces in FP64, solves the 6x6
-// system by Cholesky and composes the SE(3) update.
+// plane -> residual, pseudo-Huber weight, Jacobian -> 29 reduced terms.  Each
+// thread sums a few chunks plainly in FP32; a warp reduce-scatter then hands
+// lane l the warp's component l, which it adds to its running sum with Kahan
+// compensation; block and one-pass grid reduction follow (last-block-done
+// counter, no spinning; the last block of a pair sums the block records in
+// FP64).  k_solve then solves the 6x6 system in FP64 and composes the SE(3)
+// update.
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -190,30 +193,21 @@ __device__ __forceinline__ void accumulate_px(float2 (&t)[kPairs], float x, floa
   t[14].x += (nx != 0.f || ny != 0.f || nz != 0.f) ? 1.f : 0.f;
 }
 
-// Shared memory of one block (dynamic, > 48 KB).  Each thread owns column
-// `tid` of the staging arrays: the gathered target planes of its in-flight
-// chunks and their transformed source points (x, y, z, target index bits).
 // Depth of the per-thread staging ring: a chunk's source ranges are fetched
 // kRing chunks ahead of its projection, and its target planes are gathered
 // kRing - 1 chunks ahead of its accumulation.
 #ifndef RIMG_RING
 #define RIMG_RING 2
 #endif
-#ifndef RIMG_KAHAN_CHUNKS
-#define RIMG_KAHAN_CHUNKS 1
-#endif
 constexpr int kRing = RIMG_RING;
-// Chunks summed plainly into t before each compensated (Kahan) step.
-constexpr int kKahanChunks = RIMG_KAHAN_CHUNKS;
 
-// Shared memory of one block (dynamic, > 48 KB).  Each thread owns column
-// `tid` of the staging arrays: for each ring slot, the source ranges of one
-// 4-pixel chunk, its transformed points (x, y, z, target-index bits) and the
-// gathered target planes.
+// Shared memory of one block (dynamic).  Each thread owns column `tid` of the
+// staging arrays: for each ring slot, the source ranges of one 4-pixel chunk
+// and the gathered target planes.  The chunk's transformed points stay in
+// registers.
 template <int THREADS>
 struct IcpSmem {
   float4 src[kRing][THREADS];
-  float4 pts[kRing][4][THREADS];
   float4 planes[kRing][4][THREADS];
   float4 T4[3];                            // pose rows (R | t) in FP32
   float red[THREADS / 32][2 * kPairs];     // per-warp sums
@@ -221,11 +215,49 @@ struct IcpSmem {
   int last;
 };
 
+// Chunks summed plainly per thread between two compensated warp steps.
+#ifndef RIMG_WARP_FLUSH
+#define RIMG_WARP_FLUSH 4
+#endif
+constexpr int kWarpFlush = RIMG_WARP_FLUSH;
+
+// Reduce-scatter of the 30 lanes of t (15 float2, padded to 16) across the
+// warp: lane l receives the warp's sum of component l (component f is lane
+// f % 2 of float2 f / 2).  Recursive halving: at offset o each lane keeps the
+// half of its remaining values selected by bit o of its lane id and adds the
+// partner's copy of that half.
+__device__ __forceinline__ float warp_scatter_sum(const float2 (&t)[kPairs], int lane) {
+  float2 v[16];
+#pragma unroll
+  for (int i = 0; i < kPairs; ++i) v[i] = t[i];
+  v[15] = f2(0.f, 0.f);
+#pragma unroll
+  for (int half = 8; half >= 1; half >>= 1) {
+    const bool hi = (lane & (2 * half)) != 0;      // offsets 16, 8, 4, 2
+#pragma unroll
+    for (int j = 0; j < half; ++j) {
+      const float2 keep = hi ? v[half + j] : v[j];
+      const float2 send = hi ? v[j] : v[half + j];
+      const float2 recv = f2(__shfl_xor_sync(0xffffffffu, send.x, 2 * half),
+                             __shfl_xor_sync(0xffffffffu, send.y, 2 * half));
+      v[j] = add2(keep, recv);
+    }
+  }
+  const bool odd = lane & 1;
+  const float keep = odd ? v[0].y : v[0].x;
+  const float send = odd ? v[0].x : v[0].y;
+  return keep + __shfl_xor_sync(0xffffffffu, send, 1);
+}
+
+#ifndef RIMG_ICP_THREADS_PER_SM
+#define RIMG_ICP_THREADS_PER_SM 512
+#endif
 template <bool R0, bool GATE, bool ASSOC, bool KAHAN, int THREADS>
-__global__ void __launch_bounds__(THREADS, 512 / THREADS) k_icp(IcpLaunch a) {
+__global__ void __launch_bounds__(THREADS, RIMG_ICP_THREADS_PER_SM / THREADS) k_icp(IcpLaunch a) {
   extern __shared__ float4 smem_raw[];
   IcpSmem<THREADS>& sm = *reinterpret_cast<IcpSmem<THREADS>*>(smem_raw);
   const int tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
   const int pair = blockIdx.x / a.bpp;
   const int blk = blockIdx.x - pair * a.bpp;
   if (tid < 12) reinterpret_cast<float*>(sm.T4)[tid] = (float)a.pose[pair * 16 + tid];
@@ -242,9 +274,11 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS) k_icp(IcpLaunch a) {
   const float inv_delta = a.huber_delta > 0.f ? 1.f / a.huber_delta : 0.f;
   const float gate2 = a.max_corr_dist * a.max_corr_dist;
 
-  float2 s[kPairs], c[kPairs], t[kPairs];
+  float2 t[kPairs];
 #pragma unroll
-  for (int i = 0; i < kPairs; ++i) { s[i] = f2(0.f, 0.f); c[i] = f2(0.f, 0.f); t[i] = f2(0.f, 0.f); }
+  for (int i = 0; i < kPairs; ++i) t[i] = f2(0.f, 0.f);
+  // this lane's component of the warp's running sum, with its Kahan term
+  float ks = 0.f, kc = 0.f;
 
   // This thread's chunks: the j-th is block chunk tid + j * THREADS of the
   // block's rows [v_begin, v_end).  Cursors walk (row, 4-pixel column) one
@@ -254,6 +288,8 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS) k_icp(IcpLaunch a) {
   const int v_end = min(H, v_begin + a.rows_per_block);
   const int nchunks = max(0, v_end - v_begin) * cpr;
   const int nmine = (tid < nchunks) ? (nchunks - 1 - tid) / THREADS + 1 : 0;
+  // the warp's trip count: its first lane has the most chunks
+  const int nwarp = __shfl_sync(0xffffffffu, nmine, 0);
   const int dv = THREADS / cpr, dcu = THREADS - dv * cpr;
   struct Cursor {
     int v, cu;
@@ -271,9 +307,15 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS) k_icp(IcpLaunch a) {
     advance(cf);
   };
 
-  // Unproject, transform and project the next chunk; start the gathers of its
-  // target planes (zero-filled when the pixel has no association).
-  auto issue = [&](int slot) {
+  struct Pts {
+    float x[4], y[4], z[4];
+    int idx[4];
+  };
+
+  // Unproject, transform and project the next chunk into P; start the
+  // gathers of its target planes (zero-filled when the pixel has no
+  // association).
+  auto issue = [&](int slot, Pts& P) {
     const int v = ci.v, u0 = ci.cu << 2;
     advance(ci);
     const float4 r4 = sm.src[slot][tid];
@@ -301,64 +343,66 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS) k_icp(IcpLaunch a) {
       const bool ok = valid && fov;
       const int idx = vv * D.W + uu;
       cp_async16_zfill(&sm.planes[slot][q][tid], planes + idx, ok);
-      sm.pts[slot][q][tid] = make_float4(X, Y, Z, __int_as_float(ok ? idx : -1));
+      P.x[q] = X;
+      P.y[q] = Y;
+      P.z[q] = Z;
+      P.idx[q] = ok ? idx : -1;
     }
   };
 
-  // Add t to the running sums with Kahan compensation.
-  auto flush = [&]() {
+  // The warp's plain sums since the last step, added to each lane's running
+  // component with Kahan compensation (or plainly); t restarts at zero.
+  auto warp_flush = [&]() {
+    const float y0 = warp_scatter_sum(t, lane);
+    if (KAHAN) {
+      const float y = y0 - kc;
+      const float tt = ks + y;
+      kc = (tt - ks) - y;
+      ks = tt;
+    } else {
+      ks += y0;
+    }
 #pragma unroll
-    for (int i = 0; i < kPairs; ++i) {
-      if (KAHAN) {
-        const float2 y = sub2(t[i], c[i]);
-        const float2 tt = add2(s[i], y);
-        c[i] = sub2(sub2(tt, s[i]), y);
-        s[i] = tt;
-      } else {
-        s[i] = add2(s[i], t[i]);
-      }
-      t[i] = f2(0.f, 0.f);
-    }
+    for (int i = 0; i < kPairs; ++i) t[i] = f2(0.f, 0.f);
   };
 
-  // Accumulate the oldest chunk in flight (its planes have landed) into t.
-  auto consume = [&](int slot) {
+  // Accumulate a chunk in flight (its planes have landed) into t.
+  auto consume = [&](int slot, const Pts& P) {
     int out_idx[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       float4 pl = sm.planes[slot][q][tid];
-      const float4 P = sm.pts[slot][q][tid];
-      const int idx = __float_as_int(P.w);
+      const int idx = P.idx[q];
       if (GATE) {
         bool keep = idx >= 0;
         if (keep) {
           const int vv = idx / D.W, uu = idx - vv * D.W;
           const float rq = __ldg(drange + idx);
           const float3 qq = unproject_px(D, uu, vv, range_ok(rq) ? rq : 0.f);
-          const float dx = P.x - qq.x, dy = P.y - qq.y, dz = P.z - qq.z;
+          const float dx = P.x[q] - qq.x, dy = P.y[q] - qq.y, dz = P.z[q] - qq.z;
           keep = range_ok(rq) && (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= gate2);
         }
         if (!keep) pl = make_float4(0.f, 0.f, 0.f, 0.f);
       }
       out_idx[q] = (pl.x != 0.f || pl.y != 0.f || pl.z != 0.f) ? idx : -1;
-      accumulate_px(t, P.x, P.y, P.z, pl, inv_delta);
+      accumulate_px(t, P.x[q], P.y[q], P.z[q], pl, inv_delta);
     }
     if (ASSOC) {
       int* ap = a.assoc + pair * Ns + (long long)cc.v * W + (cc.cu << 2);
       *reinterpret_cast<int4*>(ap) = make_int4(out_idx[0], out_idx[1], out_idx[2], out_idx[3]);
       advance(cc);
     }
-    if (kKahanChunks == 1) flush();
   };
 
-  // Software pipeline over this thread's chunks with a two-slot ring (each
-  // thread reads only its own staging slots, so no block barrier is needed):
-  // step i projects chunk i (ranges fetched two steps earlier), starts its
-  // gathers and the range fetch of chunk i + 2 into the same slot, commits
-  // one cp.async group, waits until at most one group is pending (so group
-  // i - 1 -- gathers of chunk i - 1 and ranges of chunk i + 1 -- has landed)
-  // and accumulates chunk i - 1.  Unrolled by two so slots are constants.
+  // Software pipeline over the warp's chunks (warp-uniform trip count; a lane
+  // past its own last chunk only takes part in the warp steps) with a
+  // two-slot ring: step i projects chunk i (ranges fetched two steps
+  // earlier), starts its gathers and the range fetch of chunk i + 2 into the
+  // same slot, commits one cp.async group, waits until at most one group is
+  // pending (so group i - 1 has landed) and accumulates chunk i - 1.
+  // Unrolled by two so slots are constants.
   static_assert(kRing == 2, "the pipeline below is written for a two-slot ring");
+  Pts P0, P1;
   if (nmine > 0) fetch_src(0);
   if (nmine > 1) fetch_src(1);
   cp_async_commit();
@@ -367,40 +411,32 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS) k_icp(IcpLaunch a) {
   while (true) {
     // even step: slot 0 issues, slot 1 is consumed
     if (i < nmine) {
-      issue(0);
+      issue(0, P0);
       if (i + 2 < nmine) fetch_src(0);
     }
     cp_async_commit();
     asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-    if (i >= 1) consume(1);
-    if (i >= nmine) break;
+    if (i >= 1 && i - 1 < nmine) consume(1, P1);
+    if (i >= 1 && (i % kWarpFlush) == 0) warp_flush();
+    if (i >= nwarp) break;
     ++i;
     // odd step: slot 1 issues, slot 0 is consumed
     if (i < nmine) {
-      issue(1);
+      issue(1, P1);
       if (i + 2 < nmine) fetch_src(1);
     }
     cp_async_commit();
     asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-    consume(0);
-    if (i >= nmine) break;
+    if (i - 1 < nmine) consume(0, P0);
+    if ((i % kWarpFlush) == 0) warp_flush();
+    if (i >= nwarp) break;
     ++i;
   }
-  flush();
+  warp_flush();
   asm volatile("cp.async.wait_all;\n" ::: "memory");
 
-  // thread sums -> warp tree -> block (FP32)
-  const int lane = tid & 31, warp = tid >> 5;
-#pragma unroll
-  for (int i = 0; i < kPairs; ++i) {
-    float2 val = KAHAN ? sub2(s[i], c[i]) : s[i];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const float2 other = f2(__shfl_xor_sync(0xffffffffu, val.x, o), __shfl_xor_sync(0xffffffffu, val.y, o));
-      val = add2(val, other);
-    }
-    if (lane == 0) { sm.red[warp][2 * i] = val.x; sm.red[warp][2 * i + 1] = val.y; }
-  }
+  // lane l holds the warp's component l -> block (FP32)
+  if (lane < 2 * kPairs) sm.red[warp][lane] = KAHAN ? ks - kc : ks;
   __syncthreads();
   if (a.bpp == 1) {
     // one block per pair: the block total is the pair total
