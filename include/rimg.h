@@ -67,7 +67,9 @@ typedef struct rimg_level {
   size_t off_rank;          /* int[H]:    row of the j-th smallest elevation */
   size_t off_bnd;           /* float[H-1]: sin of the mid-elevation between ranks j, j+1 */
   size_t off_bins;          /* int4[n_bins]: row below / row above the bin's boundary, the
-                               boundary (float bits, +inf if none), rank at the lower edge */
+                               boundary (float bits, +inf if none; with tie_up the largest
+                               float below it, so that one "s > boundary" test applies the
+                               lower-row tie rule), rank at the lower edge */
 } rimg_level;
 
 /* A sensor's intrinsics in device form: the elevation table phi_lut and the

@@ -615,6 +615,9 @@ int rimg_sensor_build(int H, int W, int levels, const double* phi_lut, const dou
       while (j + inside < Hl - 1 && (double)bnd[j + inside] < e1) ++inside;
       if (inside > 1) exact = false;
       float bb = (inside >= 1) ? bnd[j] : INFINITY;
+      // the device tests s > bb; with tie_up a tie goes to the row above the
+      // boundary, i.e. s >= bnd, which is s > (the largest float below bnd)
+      if (desc && inside >= 1) bb = std::nextafter(bb, -INFINITY);
       int bits;
       std::memcpy(&bits, &bb, sizeof(bits));
       bins[b] = make_int4(rank[j], rank[std::min(j + 1, Hl - 1)], bits, j);

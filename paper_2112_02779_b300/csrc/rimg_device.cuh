@@ -21,18 +21,14 @@ __device__ __forceinline__ float3 unproject_px(const DevLevel& L, int u, int v, 
 // Eq. 4 in sin(elevation) space: the row whose elevation is nearest to that
 // of a point with sin(elevation) = s.  Each bin of the inverse table holds at
 // most one mid-elevation boundary (bins_exact), so one comparison with it
-// picks the row below or above; the tie rule sends exact ties to the lower
-// row index.  For tables too uneven for that, the walk across the sorted
-// boundaries (bounded by H) gives the same argmin.
+// picks the row below or above; the tie rule (exact ties go to the lower row
+// index) is folded into the stored boundary.  For tables too uneven for that,
+// the walk across the sorted boundaries (bounded by H) gives the same argmin.
 __device__ __forceinline__ int row_from_sin(const DevLevel& L, float s) {
   int b = __float2int_rd((s - L.s_lo) * L.bin_scale);
   b = min(max(b, 0), L.n_bins - 1);
   const int4 e = __ldg(L.bins + b);
-  if (L.bins_exact) {
-    const float bb = __int_as_float(e.z);
-    const bool above = L.tie_up ? (s >= bb) : (s > bb);
-    return above ? e.y : e.x;
-  }
+  if (L.bins_exact) return (s > __int_as_float(e.z)) ? e.y : e.x;   // tie rule folded into the boundary
   int j = e.w;
   if (L.tie_up) {
     for (int k = 0; k < L.H && j < L.H - 1 && s >= __ldg(L.bnd + j); ++k) ++j;
@@ -85,18 +81,19 @@ __device__ __forceinline__ int wrap_col(float uc, int W) {
 template <bool R0>
 __device__ __forceinline__ bool project_px(const DevLevel& L, float3 x, int proj_iters, int& u, int& v,
                                            float& r) {
-  float s, uc;
+  float s;
   if (!R0) {
     const float n2 = fmaf(x.x, x.x, fmaf(x.y, x.y, x.z * x.z));
     const float inv = rsqrtf(n2);
     s = x.z * inv;
     r = n2 * inv;
     v = row_from_sin(L, s);
-    uc = atan2_poly(x.y, x.x) * L.w_over_2pi;
+    float uc = atan2_poly(x.y, x.x) * L.w_over_2pi;
     if (L.has_theta) uc -= __ldg(L.thu + v);
+    u = wrap_col(uc, L.W);
   } else {
     // receiver-offset fixed point on the column angle 2 pi u_c / W
-    uc = atan2_poly(x.y, x.x) * L.w_over_2pi;
+    float uc = atan2_poly(x.y, x.x) * L.w_over_2pi;
     s = 0.f;
     r = 0.f;
     v = 0;
@@ -113,8 +110,8 @@ __device__ __forceinline__ bool project_px(const DevLevel& L, float3 x, int proj
       uc = atan2_poly(yp, xp) * L.w_over_2pi;
       if (L.has_theta) uc -= __ldg(L.thu + v);
     }
+    u = wrap_col(uc, L.W);
   }
-  u = wrap_col(uc, L.W);
   return (s >= L.s_lo) && (s <= L.s_hi);   // false for NaN
 }
 
