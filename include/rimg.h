@@ -518,8 +518,9 @@ int rimg_cnn_train_step(void* state, size_t state_bytes, int n, int H, int W, in
  * caller take the union of intervals.
  * Kernel ids: 0 unproject, 1 pyramid, 2 normals (+ plane pyramid),
  * 3 icp step (association + reduction), 4 source-range pyramid, 5 FP64
- * solve + pose update, 6 SDF integration, 7 point-cloud projection.  Not for
- * use during stream capture.
+ * solve + pose update, 6 SDF integration, 7 point-cloud projection, 8 all
+ * iterations of a small pyramid level (one block per pair).  Not for use
+ * during stream capture.
  * ------------------------------------------------------------------------- */
 int rimg_profile_begin(int max_launches);
 int rimg_profile_end(int cap, int* kernel_id, int* level, int* n_pairs, float* start_ms, float* ms);

@@ -252,17 +252,14 @@ __device__ __forceinline__ float warp_scatter_sum(const float2 (&t)[kPairs], int
 #ifndef RIMG_ICP_THREADS_PER_SM
 #define RIMG_ICP_THREADS_PER_SM 512
 #endif
+// One block's share of a step: the rows [v_begin, v_end) of pair `pair` at
+// the pose in sm.T4.  On return (after a block barrier) sm.red[w][l] holds
+// warp w's component l of the 29 sums (lane order, see kFlat).
 template <bool R0, bool GATE, bool ASSOC, bool KAHAN, int THREADS>
-__global__ void __launch_bounds__(THREADS, RIMG_ICP_THREADS_PER_SM / THREADS) k_icp(IcpLaunch a) {
-  extern __shared__ float4 smem_raw[];
-  IcpSmem<THREADS>& sm = *reinterpret_cast<IcpSmem<THREADS>*>(smem_raw);
+__device__ __forceinline__ void icp_block_terms(const IcpLaunch& a, IcpSmem<THREADS>& sm, int pair, int v_begin,
+                                                int v_end) {
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
-  const int pair = blockIdx.x / a.bpp;
-  const int blk = blockIdx.x - pair * a.bpp;
-  if (tid < 12) reinterpret_cast<float*>(sm.T4)[tid] = (float)a.pose[pair * 16 + tid];
-  __syncthreads();
-
   const DevLevel& S = a.src;
   const DevLevel& D = a.dst;
   const int W = S.W, H = S.H;
@@ -284,8 +281,6 @@ __global__ void __launch_bounds__(THREADS, RIMG_ICP_THREADS_PER_SM / THREADS) k_
   // block's rows [v_begin, v_end).  Cursors walk (row, 4-pixel column) one
   // thread-stride at a time.
   const int cpr = W >> 2;
-  const int v_begin = blk * a.rows_per_block;
-  const int v_end = min(H, v_begin + a.rows_per_block);
   const int nchunks = max(0, v_end - v_begin) * cpr;
   const int nmine = (tid < nchunks) ? (nchunks - 1 - tid) / THREADS + 1 : 0;
   // the warp's trip count: its first lane has the most chunks
@@ -435,28 +430,42 @@ __global__ void __launch_bounds__(THREADS, RIMG_ICP_THREADS_PER_SM / THREADS) k_
   warp_flush();
   asm volatile("cp.async.wait_all;\n" ::: "memory");
 
-  // lane l holds the warp's component l -> block (FP32)
+  // lane l holds the warp's component l
   if (lane < 2 * kPairs) sm.red[warp][lane] = KAHAN ? ks - kc : ks;
   __syncthreads();
+}
+
+// Block's FP32 total of reduced quantity `tid` (output order) from the
+// per-warp components.
+template <int THREADS>
+__device__ __forceinline__ float block_total(const IcpSmem<THREADS>& sm, int tid) {
+  const int f = kFlat[tid];
+  float acc = 0.f;
+#pragma unroll
+  for (int w = 0; w < THREADS / 32; ++w) acc += sm.red[w][f];
+  return acc;
+}
+
+template <bool R0, bool GATE, bool ASSOC, bool KAHAN, int THREADS>
+__global__ void __launch_bounds__(THREADS, RIMG_ICP_THREADS_PER_SM / THREADS) k_icp(IcpLaunch a) {
+  extern __shared__ float4 smem_raw[];
+  IcpSmem<THREADS>& sm = *reinterpret_cast<IcpSmem<THREADS>*>(smem_raw);
+  const int tid = threadIdx.x;
+  const int pair = blockIdx.x / a.bpp;
+  const int blk = blockIdx.x - pair * a.bpp;
+  if (tid < 12) reinterpret_cast<float*>(sm.T4)[tid] = (float)a.pose[pair * 16 + tid];
+  __syncthreads();
+  const int v_begin = blk * a.rows_per_block;
+  icp_block_terms<R0, GATE, ASSOC, KAHAN, THREADS>(a, sm, pair, v_begin, min(a.src.H, v_begin + a.rows_per_block));
   if (a.bpp == 1) {
     // one block per pair: the block total is the pair total
     if (tid < kRed) {
-      const int f = kFlat[tid];
-      float acc = 0.f;
-#pragma unroll
-      for (int w = 0; w < THREADS / 32; ++w) acc += sm.red[w][f];
-      const double v = (double)acc;
+      const double v = (double)block_total(sm, tid);
       a.sums[pair * kRedStride + tid] = v;
       if (a.out29) a.out29[pair * kRed + tid] = v;
     }
   } else {
-    if (tid < kRed) {
-      const int f = kFlat[tid];
-      float acc = 0.f;
-#pragma unroll
-      for (int w = 0; w < THREADS / 32; ++w) acc += sm.red[w][f];
-      a.partials[((long long)pair * a.bpp + blk) * kRedStride + tid] = acc;
-    }
+    if (tid < kRed) a.partials[((long long)pair * a.bpp + blk) * kRedStride + tid] = block_total(sm, tid);
     __threadfence();
     __syncthreads();
     if (tid == 0) {
@@ -478,16 +487,12 @@ __global__ void __launch_bounds__(THREADS, RIMG_ICP_THREADS_PER_SM / THREADS) k_
   }
 }
 
-// The Gauss-Newton update of every pair from its FP64 sums: one thread per
-// pair (FP64 Cholesky-type solve of the 6x6 system and the SE(3) composition).
-// Kept out of k_icp so that no reduction block holds an SM slot through the
-// serial FP64 chain.  The pair's record keeps the size of the step in its
-// spare slots: [29] |omega| (rad), [30] |tau| (m), [31] 1 if applied.
-__global__ void __launch_bounds__(32) k_solve(int n_pairs, double* __restrict__ sums,
-                                             double* __restrict__ pose, int* __restrict__ status) {
-  const int pair = blockIdx.x * blockDim.x + threadIdx.x;
-  if (pair >= n_pairs) return;
-  double* t = sums + (long long)pair * kRedStride;
+// The Gauss-Newton update from a pair's FP64 sums t[0..28]: FP64
+// Cholesky-type solve of the 6x6 system and T <- Exp(xi) T for the 3x4 pose
+// T; t[29], t[30] receive |omega| (rad) and |tau| (m) of the step and t[31]
+// 1 if it was applied (0: fewer than 6 correspondences or a degenerate pivot,
+// T unchanged).  Returns whether it was applied.
+__device__ bool solve_and_update(double* t, double* T) {
   double Hm[6][6], g[6], x[6];
   int q = 0;
   for (int i = 0; i < 6; ++i)
@@ -496,11 +501,7 @@ __global__ void __launch_bounds__(32) k_solve(int n_pairs, double* __restrict__ 
   bool good = t[28] >= 6.0;
   if (good) good = chol6_solve(Hm, g, x);
   if (good) {
-    double T[12];
-    double* P = pose + (long long)pair * 16;
-    for (int k = 0; k < 12; ++k) T[k] = P[k];
     se3_left_update(T, x);
-    for (int k = 0; k < 12; ++k) P[k] = T[k];
     t[29] = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
     t[30] = sqrt(x[3] * x[3] + x[4] * x[4] + x[5] * x[5]);
     t[31] = 1.0;
@@ -508,8 +509,62 @@ __global__ void __launch_bounds__(32) k_solve(int n_pairs, double* __restrict__ 
     t[29] = 0.0;
     t[30] = 0.0;
     t[31] = 0.0;
-    if (status) status[pair] |= RIMG_FLAG_DEGENERATE;
   }
+  return good;
+}
+
+// The Gauss-Newton update of every pair from its FP64 sums: one thread per
+// pair.  Kept out of k_icp so that no reduction block holds an SM slot
+// through the serial FP64 chain.  The pair's record keeps the size of the
+// step in its spare slots.
+__global__ void __launch_bounds__(32) k_solve(int n_pairs, double* __restrict__ sums,
+                                             double* __restrict__ pose, int* __restrict__ status) {
+  const int pair = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pair >= n_pairs) return;
+  double T[12];
+  double* P = pose + (long long)pair * 16;
+  for (int k = 0; k < 12; ++k) T[k] = P[k];
+  if (solve_and_update(sums + (long long)pair * kRedStride, T)) {
+    for (int k = 0; k < 12; ++k) P[k] = T[k];
+  } else if (status) {
+    status[pair] |= RIMG_FLAG_DEGENERATE;
+  }
+}
+
+// All iterations of one small level in one launch: one block per pair
+// associates and reduces the pair's whole level, its first thread solves in
+// FP64 and updates the pose in shared memory, and the block goes on with the
+// next iteration -- the per-iteration launches (association + solve) of a
+// level whose pair fits one block collapse into one.  Same arithmetic as
+// k_icp with one block per pair followed by k_solve.  The pair's final sums
+// and step record are left in a.sums (as after the last k_solve).
+template <bool R0, bool GATE, bool KAHAN, int THREADS>
+__global__ void __launch_bounds__(THREADS, RIMG_ICP_THREADS_PER_SM / THREADS) k_icp_iters(IcpLaunch a, int iters) {
+  extern __shared__ float4 smem_raw[];
+  IcpSmem<THREADS>& sm = *reinterpret_cast<IcpSmem<THREADS>*>(smem_raw);
+  __shared__ double Tp[12];
+  __shared__ int degenerate;
+  const int tid = threadIdx.x;
+  const int pair = blockIdx.x;
+  if (tid < 12) {
+    Tp[tid] = a.pose[pair * 16 + tid];
+    reinterpret_cast<float*>(sm.T4)[tid] = (float)Tp[tid];
+  }
+  if (tid == 0) degenerate = 0;
+  __syncthreads();
+  for (int it = 0; it < iters; ++it) {
+    icp_block_terms<R0, GATE, false, KAHAN, THREADS>(a, sm, pair, 0, a.src.H);
+    if (tid < kRed) sm.tot[tid] = (double)block_total(sm, tid);
+    __syncthreads();
+    if (tid == 0) {
+      if (!solve_and_update(sm.tot, Tp)) degenerate = 1;
+      for (int k = 0; k < 12; ++k) reinterpret_cast<float*>(sm.T4)[k] = (float)Tp[k];
+    }
+    __syncthreads();
+  }
+  if (tid < 12) a.pose[pair * 16 + tid] = Tp[tid];
+  if (iters > 0 && tid < kRedStride) a.sums[pair * kRedStride + tid] = sm.tot[tid];
+  if (tid == 0 && degenerate && a.status) a.status[pair] |= RIMG_FLAG_DEGENERATE;
 }
 
 cudaError_t launch_solve(int n_pairs, double* sums, double* pose, int* status, cudaStream_t st) {
@@ -612,6 +667,45 @@ template <bool R0, bool GATE, bool ASSOC, bool KAHAN>
 cudaError_t launch_icp_k(const IcpLaunch& a, long long blocks, cudaStream_t st) {
   return a.threads == 128 ? launch_icp_t<R0, GATE, ASSOC, KAHAN, 128>(a, blocks, st)
                           : launch_icp_t<R0, GATE, ASSOC, KAHAN, 256>(a, blocks, st);
+}
+
+template <bool R0, bool GATE, bool KAHAN, int T>
+cudaError_t launch_icp_iters_t(const IcpLaunch& a, int iters, cudaStream_t st) {
+  constexpr size_t bytes = sizeof(IcpSmem<T>);
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_icp_iters<R0, GATE, KAHAN, T>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  k_icp_iters<R0, GATE, KAHAN, T><<<(unsigned)a.n_pairs, T, bytes, st>>>(a, iters);
+  return cudaGetLastError();
+}
+
+template <bool R0, bool GATE, bool KAHAN>
+cudaError_t launch_icp_iters_k(const IcpLaunch& a, int iters, cudaStream_t st) {
+  return a.threads == 128 ? launch_icp_iters_t<R0, GATE, KAHAN, 128>(a, iters, st)
+                          : launch_icp_iters_t<R0, GATE, KAHAN, 256>(a, iters, st);
+}
+
+bool icp_iters_fits(int H, int W) { return (long long)H * (W / 4) <= kIcpItersMaxChunks; }
+
+cudaError_t launch_icp_iters(IcpLaunch a, int iters, cudaStream_t st) {
+  if (a.n_pairs == 0 || iters == 0) return cudaSuccess;
+  const long long chunks = (long long)a.src.H * (a.src.W / 4);
+  a.threads = chunks <= 512 ? 128 : 256;
+  a.bpp = 1;
+  a.rows_per_block = a.src.H;
+  const bool r0 = a.dst.r0 != 0.f || a.src.r0 != 0.f;
+  const bool gate = a.max_corr_dist > 0.f;
+  const bool kahan = a.kahan != 0;
+  if (r0) {
+    if (gate) return kahan ? launch_icp_iters_k<true, true, true>(a, iters, st) : launch_icp_iters_k<true, true, false>(a, iters, st);
+    return kahan ? launch_icp_iters_k<true, false, true>(a, iters, st) : launch_icp_iters_k<true, false, false>(a, iters, st);
+  }
+  if (gate) return kahan ? launch_icp_iters_k<false, true, true>(a, iters, st) : launch_icp_iters_k<false, true, false>(a, iters, st);
+  return kahan ? launch_icp_iters_k<false, false, true>(a, iters, st) : launch_icp_iters_k<false, false, false>(a, iters, st);
 }
 
 cudaError_t launch_icp(const IcpLaunch& a, cudaStream_t st) {

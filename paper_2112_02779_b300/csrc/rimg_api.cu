@@ -239,6 +239,36 @@ int icp_launch(const rimg_sensor* src, const rimg_sensor* dst, int level, int n_
   return RIMG_OK;
 }
 
+// All `iters` Gauss-Newton steps of a small level in one launch (one block
+// per pair; see k_icp_iters).
+int icp_iters_launch(const rimg_sensor* src, const rimg_sensor* dst, int level, int n_pairs,
+                     const float* src_range_l, const float* dst_planes_l, const float* dst_range_l, double* pose,
+                     const rimg_params* p, int* status, const IcpScratch& w, int iters, cudaStream_t st) {
+  if (p->max_corr_dist > 0.f && !dst_range_l) return RIMG_ERR_INVALID_ARG;
+  IcpLaunch a{};
+  a.src = dev_level(src, level);
+  a.dst = dev_level(dst, level);
+  a.n_pairs = n_pairs;
+  a.src_range = src_range_l;
+  a.dst_planes = reinterpret_cast<const float4*>(dst_planes_l);
+  a.dst_range = dst_range_l;
+  a.pose = pose;
+  a.status = status;
+  a.partials = w.partials;
+  a.counters = w.counters;
+  a.sums = w.sums;
+  a.huber_delta = p->huber_delta;
+  a.max_corr_dist = p->max_corr_dist;
+  a.proj_iters = p->proj_iters;
+  a.kahan = p->kahan;
+  a.update = 1;
+  prof_before(st, K_ICP_ITERS, level, n_pairs);
+  cudaError_t e = launch_icp_iters(a, iters, st);
+  prof_after(st);
+  if (e != cudaSuccess) return cuda_fail(e, "icp iterations kernel");
+  return RIMG_OK;
+}
+
 // Per-level buffers of the pairs [p0, p0 + n) of a registration workspace.
 struct SliceBufs {
   float* planes[RIMG_MAX_LEVELS];
@@ -319,6 +349,11 @@ int register_slice(const rimg_sensor* src, const rimg_sensor* dst, int p0, int n
     const int l = levels - 1 - k;
     const float* s_l = (l == 0) ? src_range : srcl[l];
     const float* d_l = gate ? ((l == 0) ? dst_range : dstl[l]) : nullptr;
+    if (iters[k] > 0 && icp_iters_fits(H >> l, W >> l)) {
+      int rc = icp_iters_launch(src, dst, l, n, s_l, planes[l], d_l, T_out, p, status, scr, iters[k], st);
+      if (rc) return rc;
+      continue;
+    }
     for (int it = 0; it < iters[k]; ++it) {
       int rc = icp_launch(src, dst, l, n, s_l, planes[l], d_l, T_out, p, 1, nullptr, nullptr, status, scr, st);
       if (rc) return rc;

@@ -23,7 +23,7 @@ struct DevLevel {
 
 DevLevel dev_level(const rimg_sensor* s, int level);
 
-enum KernelId { K_UNPROJECT = 0, K_PYRAMID = 1, K_NORMALS = 2, K_ICP = 3, K_SRC_PYRAMID = 4, K_SOLVE = 5, K_SDF = 6, K_POINTS = 7 };
+enum KernelId { K_UNPROJECT = 0, K_PYRAMID = 1, K_NORMALS = 2, K_ICP = 3, K_SRC_PYRAMID = 4, K_SOLVE = 5, K_SDF = 6, K_POINTS = 7, K_ICP_ITERS = 8 };
 
 // Launch-timing hooks (no-ops unless rimg_profile_begin was called).
 void prof_before(cudaStream_t st, int kernel, int level, int n);
@@ -63,6 +63,11 @@ void icp_tune_clear();
 int icp_tune_size();
 cudaError_t launch_icp(const IcpLaunch& a, cudaStream_t st);
 cudaError_t launch_solve(int n_pairs, double* sums, double* pose, int* status, cudaStream_t st);
+// All iterations of a level whose pair fits one block (H_l * W_l / 4 chunks
+// <= kIcpItersMaxChunks) in one launch; a.pose is updated in place.
+constexpr int kIcpItersMaxChunks = 1024;
+bool icp_iters_fits(int H, int W);
+cudaError_t launch_icp_iters(IcpLaunch a, int iters, cudaStream_t st);
 
 cudaError_t launch_sdf(const DevLevel& L, int n_scans, const float* ranges, const double* poses, int nx, int ny,
                        int nz, float ox, float oy, float oz, float voxel, float trunc, int proj_iters, float* sdf,

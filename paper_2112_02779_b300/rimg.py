@@ -466,7 +466,8 @@ def rimg_profile_end(cap=100000):
     return [(kid[i], lvl[i], npr[i], t0[i], ms[i]) for i in range(n)]
 
 
-KERNEL_NAMES = {0: "unproject", 1: "pyramid", 2: "normals", 3: "icp_step", 4: "src_pyramid", 5: "solve", 6: "sdf", 7: "points"}
+KERNEL_NAMES = {0: "unproject", 1: "pyramid", 2: "normals", 3: "icp_step", 4: "src_pyramid", 5: "solve", 6: "sdf", 7: "points",
+                8: "icp_iters"}
 
 __all__ = [n for n in dir() if n.startswith("rimg_")] + ["Sensor", "Groups", "ProposalNet", "RimgError", "KERNEL_NAMES",
                                                           "RIMG_MAX_LEVELS", "RIMG_FLAG_DEGENERATE", "lib"]
