@@ -193,45 +193,60 @@ template <bool PCA>
 __global__ void __launch_bounds__(NT_X* NT_Y) k_normals(DevLevel L, int levels, int n, const float* __restrict__ range,
                                                         float rel_jump, PlaneOut out,
                                                         uint8_t* __restrict__ mask0) {
-  __shared__ float sx[NH_Y][NH_X], sy[NH_Y][NH_X], sz[NH_Y][NH_X], sr[NH_Y][NH_X];
+  __shared__ float4 sp[NH_Y][NH_X];   // point (x, y, z) and range (0: invalid) of each tile pixel
   const int img = blockIdx.z;
   const int u0 = blockIdx.x * NT_X - 1, v0 = blockIdx.y * NT_Y - 1;
   const int H = L.H, W = L.W;
   const float* rimg = range + (long long)img * H * W;
   const int tid = threadIdx.y * NT_X + threadIdx.x;
-  for (int k = tid; k < NH_X * NH_Y; k += NT_X * NT_Y) {
-    const int hy = k / NH_X, hx = k - hy * NH_X;
+  auto stage = [&](int hy, int hx) {
     const int v = v0 + hy;
-    int u = (u0 + hx) % W;          // the halo wraps around the 360 degree image
+    // the halo wraps around the 360 degree image: u0 + hx lies in [-1, W + 32],
+    // so one conditional step suffices unless the image is narrower than the tile
+    int u = u0 + hx;
     u = (u < 0) ? u + W : u;
-    float r = 0.f;
-    if (v >= 0 && v < H) r = __ldg(rimg + (long long)v * W + u);
-    const bool ok = (v >= 0 && v < H) && range_ok(r);
+    u = (u >= W) ? u - W : u;
+    if (u >= W) u %= W;
+    const bool row_in = v >= 0 && v < H;
+    const float r = row_in ? __ldg(rimg + (long long)v * W + u) : 0.f;
+    const bool ok = row_in && range_ok(r);
     float3 p = make_float3(0.f, 0.f, 0.f);
     if (ok) p = unproject_px(L, u, v, r);
-    sx[hy][hx] = p.x;
-    sy[hy][hx] = p.y;
-    sz[hy][hx] = p.z;
-    sr[hy][hx] = ok ? r : 0.f;   // 0 marks an invalid pixel
+    sp[hy][hx] = make_float4(p.x, p.y, p.z, ok ? r : 0.f);
+  };
+  // each thread stages its own pixel, then 84 threads the ring around the tile
+  // (top and bottom halo rows, left and right halo columns)
+  stage(threadIdx.y + 1, threadIdx.x + 1);
+  if (tid < 2 * NH_X + 2 * NT_Y) {
+    int hy, hx;
+    if (tid < NH_X) {
+      hy = 0; hx = tid;
+    } else if (tid < 2 * NH_X) {
+      hy = NH_Y - 1; hx = tid - NH_X;
+    } else {
+      const int k = tid - 2 * NH_X;
+      hy = 1 + (k >> 1); hx = (k & 1) ? NH_X - 1 : 0;
+    }
+    stage(hy, hx);
   }
   __syncthreads();
   const int u = blockIdx.x * NT_X + threadIdx.x;
   const int v = blockIdx.y * NT_Y + threadIdx.y;
   if (u >= W || v >= H) return;
   const int cx = threadIdx.x + 1, cy = threadIdx.y + 1;
-  const float rc = sr[cy][cx];
+  const float4 C = sp[cy][cx];
+  const float rc = C.w;
   if (PCA) {
     float q[9][3];
     bool use[9];
-    const float px = sx[cy][cx], py = sy[cy][cx], pz = sz[cy][cx];
+    const float px = C.x, py = C.y, pz = C.z;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-      const int yy = cy + i / 3 - 1, xx = cx + i % 3 - 1;
-      const float rn = sr[yy][xx];
-      use[i] = rc > 0.f && rn > 0.f && fmaf(rel_jump, rc, -fabsf(rn - rc)) >= 0.f;
-      q[i][0] = sx[yy][xx] - px;
-      q[i][1] = sy[yy][xx] - py;
-      q[i][2] = sz[yy][xx] - pz;
+      const float4 Q = sp[cy + i / 3 - 1][cx + i % 3 - 1];
+      use[i] = rc > 0.f && Q.w > 0.f && fmaf(rel_jump, rc, -fabsf(Q.w - rc)) >= 0.f;
+      q[i][0] = Q.x - px;
+      q[i][1] = Q.y - py;
+      q[i][2] = Q.z - pz;
     }
     float nx = 0.f, ny = 0.f, nz = 0.f;
     bool ok = (v > 0) && (v < H - 1) && rc > 0.f && pca_normal(q, use, nx, ny, nz);
@@ -244,17 +259,16 @@ __global__ void __launch_bounds__(NT_X* NT_Y) k_normals(DevLevel L, int levels, 
     write_plane(out, mask0, img, H, W, u, v, levels, plane, ok);
     return;
   }
-  const float rl = sr[cy][cx - 1], rr = sr[cy][cx + 1], ru = sr[cy - 1][cx], rd = sr[cy + 1][cx];
+  const float4 Pl = sp[cy][cx - 1], Pr = sp[cy][cx + 1], Pu = sp[cy - 1][cx], Pd = sp[cy + 1][cx];
+  const float rl = Pl.w, rr = Pr.w, ru = Pu.w, rd = Pd.w;
   // |r_nb - r_c| <= rel_jump * r_c decided exactly: the difference is exact
   // (Sterbenz) whenever the test can pass, and the sign of one fused
   // multiply-add is the sign of the exact value.
   bool ok = (v > 0) && (v < H - 1) && rc > 0.f && rl > 0.f && rr > 0.f && ru > 0.f && rd > 0.f;
   ok = ok && fmaf(rel_jump, rc, -fabsf(rl - rc)) >= 0.f && fmaf(rel_jump, rc, -fabsf(rr - rc)) >= 0.f &&
        fmaf(rel_jump, rc, -fabsf(ru - rc)) >= 0.f && fmaf(rel_jump, rc, -fabsf(rd - rc)) >= 0.f;
-  const float ax = sx[cy][cx + 1] - sx[cy][cx - 1], ay = sy[cy][cx + 1] - sy[cy][cx - 1],
-              az = sz[cy][cx + 1] - sz[cy][cx - 1];
-  const float bx = sx[cy + 1][cx] - sx[cy - 1][cx], by = sy[cy + 1][cx] - sy[cy - 1][cx],
-              bz = sz[cy + 1][cx] - sz[cy - 1][cx];
+  const float ax = Pr.x - Pl.x, ay = Pr.y - Pl.y, az = Pr.z - Pl.z;
+  const float bx = Pd.x - Pu.x, by = Pd.y - Pu.y, bz = Pd.z - Pu.z;
   float nx = fmaf(ay, bz, -az * by), ny = fmaf(az, bx, -ax * bz), nz = fmaf(ax, by, -ay * bx);
   const float c2 = fmaf(nx, nx, fmaf(ny, ny, nz * nz));
   const float a2 = fmaf(ax, ax, fmaf(ay, ay, az * az));
@@ -264,8 +278,7 @@ __global__ void __launch_bounds__(NT_X* NT_Y) k_normals(DevLevel L, int levels, 
   if (ok) {
     const float inv = rsqrtf(c2);
     nx *= inv; ny *= inv; nz *= inv;
-    const float px = sx[cy][cx], py = sy[cy][cx], pz = sz[cy][cx];
-    float d = fmaf(nx, px, fmaf(ny, py, nz * pz));
+    float d = fmaf(nx, C.x, fmaf(ny, C.y, nz * C.z));
     if (d > 0.f) { nx = -nx; ny = -ny; nz = -nz; d = -d; }
     plane = make_float4(nx, ny, nz, d);
   }
