@@ -694,7 +694,7 @@ bool icp_iters_fits(int H, int W) { return (long long)H * (W / 4) <= kIcpItersMa
 cudaError_t launch_icp_iters(IcpLaunch a, int iters, cudaStream_t st) {
   if (a.n_pairs == 0 || iters == 0) return cudaSuccess;
   const long long chunks = (long long)a.src.H * (a.src.W / 4);
-  a.threads = chunks <= 512 ? 128 : 256;
+  a.threads = chunks <= 512 ? 128 : 256;      // 4 chunks per thread at most with 128 threads
   a.bpp = 1;
   a.rows_per_block = a.src.H;
   const bool r0 = a.dst.r0 != 0.f || a.src.r0 != 0.f;

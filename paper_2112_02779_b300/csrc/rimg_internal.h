@@ -64,8 +64,9 @@ int icp_tune_size();
 cudaError_t launch_icp(const IcpLaunch& a, cudaStream_t st);
 cudaError_t launch_solve(int n_pairs, double* sums, double* pose, int* status, cudaStream_t st);
 // All iterations of a level whose pair fits one block (H_l * W_l / 4 chunks
-// <= kIcpItersMaxChunks) in one launch; a.pose is updated in place.
-constexpr int kIcpItersMaxChunks = 1024;
+// <= kIcpItersMaxChunks, i.e. at most 16 chunks per thread of a 256-thread
+// block) in one launch; a.pose is updated in place.
+constexpr int kIcpItersMaxChunks = 4096;
 bool icp_iters_fits(int H, int W);
 cudaError_t launch_icp_iters(IcpLaunch a, int iters, cudaStream_t st);
 
