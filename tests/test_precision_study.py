@@ -10,8 +10,8 @@ last * rho / (1 - rho), rho = last / previous (capped at 0.95), and at least
 its last step.  Projective re-association is discrete: an association that
 the FP32 path and the FP64 oracle decide differently (a near-tie, Section 4.1)
 can send a slowly converging pair to a neighbouring optimum of the same
-method; up to 1 % of the unconverged pairs may therefore exceed that bar, none
-by more than 1e-3.
+method; up to 1 % of the unconverged pairs (at least one) may therefore
+exceed that bar, none of them by more than 1e-3.
 
 By default a sample of 12 pairs runs; RIMG_PRECISION_PAIRS=200 runs the full
 study.  With RIMG_REPORT_DIR set, a JSON report with every pair's errors is
@@ -104,7 +104,7 @@ def test_precision_kahan_vs_plain_fp32():
         bar = 1e-4 + 3 * tail
         beyond = np.any(res[k] > bar, axis=1)
         assert not np.any(beyond & converged), (k, res[k][converged].max(0))
-        assert beyond.sum() <= max(0, int(0.01 * (~converged).sum())), (k, np.nonzero(beyond)[0])
-        assert res[k].max() <= 1e-3, (k, res[k].max(0))
+        assert beyond.sum() <= max(1, int(np.ceil(0.01 * (~converged).sum()))), (k, np.nonzero(beyond)[0])
+        assert np.all(res[k][beyond] <= 1e-3), (k, res[k][beyond])
         if converged.any():
             assert res[k][converged].max() <= 1e-4, (k, res[k][converged].max(0))
