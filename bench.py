@@ -271,27 +271,30 @@ def run_e2e(args, R, sens, params, cfg, src_np, dst_np, Tg, B, stream, dev, worl
     """End to end through the host-buffer entry point: every step uploads its
     two range images per pair and the initial poses from pinned host memory,
     registers, and reads its poses and status back to the host, all inside the
-    timed region.  Steps alternate two workspaces and two streams, so the
-    upload of step k+1 overlaps the registration of step k (as a streaming
-    caller would run it); the region ends after both streams are drained."""
+    timed region.  Steps rotate over three workspaces and three streams (as a
+    streaming caller would run it): step k+1's upload may overwrite a staging
+    buffer only once the step that last used it has been registered, and
+    with three buffers that is step k-2, so uploads run back to back while
+    step k registers; the region ends after all streams are drained."""
     import torch
     N0 = cfg.H * cfg.W
     hs = torch.from_numpy(src_np).pin_memory()
     hd = torch.from_numpy(dst_np).pin_memory()
     hT0 = torch.eye(4, dtype=torch.float64).reshape(1, 16).repeat(B, 1).contiguous().pin_memory()
-    hT1 = [torch.zeros((B, 16), dtype=torch.float64).pin_memory() for _ in range(2)]
-    hst = [torch.zeros(B, dtype=torch.int32).pin_memory() for _ in range(2)]
+    nbuf = 3
+    hT1 = [torch.zeros((B, 16), dtype=torch.float64).pin_memory() for _ in range(nbuf)]
+    hst = [torch.zeros(B, dtype=torch.int32).pin_memory() for _ in range(nbuf)]
     chunk = min(args.e2e_chunk, B)
     nbytes = R.rimg_register_host_workspace_bytes(sens, sens, B, cfg.levels, chunk)
-    ws_h = [torch.empty(nbytes, dtype=torch.uint8, device=dev) for _ in range(2)]
-    streams = [torch.cuda.Stream(dev) for _ in range(2)]
+    ws_h = [torch.empty(nbytes, dtype=torch.uint8, device=dev) for _ in range(nbuf)]
+    streams = [torch.cuda.Stream(dev) for _ in range(nbuf)]
 
     def run(k):
-        j = k % 2
+        j = k % nbuf
         R.rimg_register_host_async(sens, sens, B, hs, hd, hT0, hT1[j], cfg.levels, cfg.iters, params, hst[j],
                                    chunk, ws_h[j], streams[j])
 
-    for k in range(2):
+    for k in range(nbuf):
         run(k)
     for st in streams:
         st.synchronize()
@@ -308,12 +311,12 @@ def run_e2e(args, R, sens, params, cfg, src_np, dst_np, Tg, B, stream, dev, worl
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
         barrier()
-    Th = hT1[(args.steps - 1) % 2].numpy().reshape(B, 4, 4)
+    Th = hT1[(args.steps - 1) % nbuf].numpy().reshape(B, 4, 4)
     diff = max(max(pose_error(Th[i], Tg[i])) for i in range(min(B, 16)))
     return {"value": world * B * args.steps / e2e_s, "unit": "pairs/s",
             "h2d_bytes_per_step": int(B * N0 * 4 * 2 + B * 16 * 8),
             "d2h_bytes_per_step": int(B * 16 * 8 + B * 4), "chunk_pairs": chunk,
-            "pipelining": "two streams / workspaces: upload of step k+1 overlaps registration of step k",
+            "pipelining": "three streams / workspaces: uploads run back to back while earlier steps register",
             "max_pose_diff_vs_device_path": diff}
 
 
