@@ -6,7 +6,7 @@
 // compensation; block and one-pass grid reduction follow (last-block-done
 // counter, no spinning; the last block of a pair sums the block records in
 // FP64).  k_solve then solves the 6x6 system in FP64 and composes the SE(3)
-// update.
+// update, one warp per pair.
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -29,99 +29,155 @@ __device__ __forceinline__ double recip_newton(double d) {
   return x;
 }
 
-// FP64 solve of the 6x6 system H x = -g by an LDL^T (square-root-free
-// Cholesky) factorisation with one reciprocal per pivot; false on a pivot
-// <= 1e-12 * trace(H) (the same test as on the Cholesky pivots L_jj^2).
-__device__ bool chol6_solve(const double (&Hm)[6][6], const double (&g)[6], double (&x)[6]) {
-  double L[6][6], D[6], Di[6];
+constexpr unsigned kFullMask = 0xffffffffu;
+
+// Index of H_ij (i <= j) in the reduced record: the 21 upper-triangle
+// entries of J^T W J row-major (row i starts at i (11 - i) / 2).
+__device__ __forceinline__ int upper_index(int i, int j) { return i * (11 - i) / 2 + j; }
+
+// On this GPU every FP64 warp instruction occupies the sub-partition's FP64
+// pipe for a fixed number of cycles whatever the number of active lanes, so
+// the per-pair Gauss-Newton update is spread over the 32 lanes of one warp:
+// one matrix entry per lane in the solve, one pose entry per lane in the
+// update.  All lanes of the warp call these together with the same
+// arguments; results are the same in every lane.
+
+// 2^-e for the binary exponent e of x > 0: a power of two, so multiplying by
+// it is exact (exponent field clamped to the normal range).
+__device__ __forceinline__ double pow2_neg_exponent(double x) {
+  const int E = min(max((__double2hiint(x) >> 20) & 0x7ff, 1), 2045);
+  return __hiloint2double((2046 - E) << 20, 0);
+}
+// The significand of x > 0 as a number in [1, 2): x 2^-e, exactly.
+__device__ __forceinline__ double significand_of(double x) {
+  return __hiloint2double((__double2hiint(x) & 0x000fffff) | 0x3ff00000, __double2loint(x));
+}
+
+// Warp-cooperative FP64 solve of H x = -g (H from the packed upper triangle
+// t[0..20], g = t[21..26]) by right-looking symmetric Gaussian elimination,
+// i.e. LDL^T: lanes 0..20 hold the lower triangle (lane i (i + 1) / 2 + j for
+// j <= i), lanes 21..26 the right-hand side.  Step k takes pivot d_k and
+// replaces every entry below and right of it by (d_k a_ij - a_ik a_jk) 2^-e_k
+// (e_k the exponent of d_k): the standard update a_ij - a_ik a_jk / d_k times
+// s_k = d_k 2^-e_k in [1, 2), with no reciprocal on the step-to-step chain.
+// The trailing block, right-hand side included, carries the product S_k of
+// the earlier s, so the LDL^T pivot is d_k / S_k; each row of the final
+// system U x = c (row k: column k of the stored lower triangle, pivot d_k,
+// c_k) carries one common factor, which cancels in the column-oriented back
+// substitution in lanes 21..26.  False if a pivot d_k / S_k <= 1e-12 trace(H).
+__device__ bool warp_solve6(const double* t, int lane, double (&x)[6]) {
+  int i, j;   // the lane's entry; j = 6 marks the right-hand side
+  if (lane < 21) {
+    i = 0;
+    while ((i + 1) * (i + 2) / 2 <= lane) ++i;
+    j = lane - i * (i + 1) / 2;
+  } else {
+    i = lane - 21;
+    j = 6;
+  }
+  const bool rhs = lane >= 21 && lane < 27;
+  const bool live = lane < 27;
+  double v = 0.0;
+  if (lane < 21) v = t[upper_index(j, i)];
+  else if (rhs) v = -t[21 + i];
+  const int base_a = live ? i * (i + 1) / 2 : 0;              // lane of entry (i, 0)
+  const int base_b = (lane < 21) ? j * (j + 1) / 2 : 21;      // lane of (j, 0), or of c_0
+  double dk = 1.0, sk = 1.0;                                  // lane k < 6: d_k and s_k
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const double d = __shfl_sync(kFullMask, v, k * (k + 3) / 2);
+    const double sc = pow2_neg_exponent(d);
+    if (lane == k) {
+      dk = d;
+      sk = significand_of(d);
+    }
+    const double aik = __shfl_sync(kFullMask, v, (base_a + k) & 31);
+    const double ajk = __shfl_sync(kFullMask, v, (base_b + k) & 31);
+    if (live && i > k && j > k) v = fma(d, v, -(aik * ajk)) * sc;
+  }
+  // S_k = s_0 ... s_{k-1} in lane k (exclusive prefix product), then the pivot test
+  double pre = sk;
+#pragma unroll
+  for (int off = 1; off < 8; off <<= 1) {
+    const double o = __shfl_up_sync(kFullMask, pre, off);
+    if (lane >= off) pre *= o;
+  }
+  double Sk = __shfl_up_sync(kFullMask, pre, 1);
+  if (lane == 0) Sk = 1.0;
   double tr = 0.0;
 #pragma unroll
-  for (int i = 0; i < 6; ++i) tr += Hm[i][i];
-  const double eps = 1e-12 * tr;
+  for (int q = 0; q < 6; ++q) tr += t[upper_index(q, q)];
+  const bool bad = lane < 6 && !(dk > (1e-12 * tr) * Sk);
+  if (__any_sync(kFullMask, bad)) return false;
+  const double inv = recip_newton(dk);                        // 1 / d_k in lane k
 #pragma unroll
-  for (int j = 0; j < 6; ++j) {
-    double d = Hm[j][j];
-#pragma unroll
-    for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k] * D[k];
-    if (!(d > eps)) return false;
-    D[j] = d;
-    Di[j] = recip_newton(d);
-#pragma unroll
-    for (int i = j + 1; i < 6; ++i) {
-      double s = Hm[i][j];
-#pragma unroll
-      for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k] * D[k];
-      L[i][j] = s * Di[j];
-    }
-  }
-  double y[6];
-#pragma unroll
-  for (int i = 0; i < 6; ++i) {
-    double s = -g[i];
-#pragma unroll
-    for (int k = 0; k < i; ++k) s -= L[i][k] * y[k];
-    y[i] = s;
-  }
-#pragma unroll
-  for (int i = 5; i >= 0; --i) {
-    double s = y[i] * Di[i];
-#pragma unroll
-    for (int k = i + 1; k < 6; ++k) s -= L[k][i] * x[k];
-    x[i] = s;
+  for (int k = 5; k >= 0; --k) {
+    const double xk = __shfl_sync(kFullMask, v, 21 + k) * __shfl_sync(kFullMask, inv, k);
+    x[k] = xk;
+    const double u = __shfl_sync(kFullMask, v, (k * (k + 1) / 2 + (rhs ? i : 0)) & 31);
+    if (rhs && i < k) v = fma(-u, xk, v);
   }
   return true;
 }
 
-// T <- Exp(xi) T for xi = (omega, tau): Rodrigues rotation and the V matrix
-// of SE(3).  For |omega| < 0.5 rad (every Gauss-Newton step in practice) the
-// coefficients sin(t)/t, (1 - cos t)/t^2 and (t - sin t)/t^3 come from their
-// Taylor series in nested form up to t^12 (truncation < 1e-13 relative), so the
-// update needs only FP64 multiply-adds; larger rotations use sincos.
-__device__ void se3_left_update(double* T, const double (&xi)[6]) {
+__device__ __forceinline__ double pick3(int s, double a, double b, double c) { return s == 0 ? a : (s == 1 ? b : c); }
+
+// Warp-cooperative T <- Exp(xi) T for xi = (omega, tau) and the 3x4 pose T
+// (row-major; rewritten by lanes 0..11, one entry each; Tf, if given,
+// receives its FP32 copy).  Rodrigues: R = I + A K + B K^2, V = I + B K + C K^2
+// with K = [omega]_x, K^2 = omega omega^T - |omega|^2 I and A = sin(t)/t,
+// B = (1 - cos t)/t^2, C = (t - sin t)/t^3.  For |omega| < 0.5 rad (every
+// Gauss-Newton step in practice) lane s = 0, 1, 2 (mod 3) evaluates the
+// Taylor series of A, B, C in t^2 to degree 6 (coefficients (-1)^n /
+// (2n + 1 + s)!, truncation < 1e-16 relative), otherwise sincos.  Lane
+// 4r + c forms row r of R times column c of T while lane 12 + r forms row r of
+// V times tau, which lane 4r + 3 then adds to the new translation.
+__device__ void warp_se3_update(double* T, const double (&xi)[6], int lane, float* Tf) {
   const double wx = xi[0], wy = xi[1], wz = xi[2];
-  const double th2 = wx * wx + wy * wy + wz * wz;
+  const double th2 = fma(wz, wz, fma(wy, wy, wx * wx));
   double A, B, C;
   if (th2 < 0.25) {
-    A = 1.0 - th2 * (1.0 / 6.0) * (1.0 - th2 * (1.0 / 20.0) * (1.0 - th2 * (1.0 / 42.0) *
-        (1.0 - th2 * (1.0 / 72.0) * (1.0 - th2 * (1.0 / 110.0) * (1.0 - th2 * (1.0 / 156.0))))));
-    B = 0.5 * (1.0 - th2 * (1.0 / 12.0) * (1.0 - th2 * (1.0 / 30.0) * (1.0 - th2 * (1.0 / 56.0) *
-        (1.0 - th2 * (1.0 / 90.0) * (1.0 - th2 * (1.0 / 132.0) * (1.0 - th2 * (1.0 / 182.0)))))));
-    C = (1.0 / 6.0) * (1.0 - th2 * (1.0 / 20.0) * (1.0 - th2 * (1.0 / 42.0) * (1.0 - th2 * (1.0 / 72.0) *
-        (1.0 - th2 * (1.0 / 110.0) * (1.0 - th2 * (1.0 / 156.0) * (1.0 - th2 * (1.0 / 210.0)))))));
+    const int s = lane % 3;
+    double p = pick3(s, 1.0 / 6227020800.0, 1.0 / 87178291200.0, 1.0 / 1307674368000.0);
+    p = fma(p, th2, pick3(s, -1.0 / 39916800.0, -1.0 / 479001600.0, -1.0 / 6227020800.0));
+    p = fma(p, th2, pick3(s, 1.0 / 362880.0, 1.0 / 3628800.0, 1.0 / 39916800.0));
+    p = fma(p, th2, pick3(s, -1.0 / 5040.0, -1.0 / 40320.0, -1.0 / 362880.0));
+    p = fma(p, th2, pick3(s, 1.0 / 120.0, 1.0 / 720.0, 1.0 / 5040.0));
+    p = fma(p, th2, pick3(s, -1.0 / 6.0, -1.0 / 24.0, -1.0 / 120.0));
+    p = fma(p, th2, pick3(s, 1.0, 0.5, 1.0 / 6.0));
+    A = __shfl_sync(kFullMask, p, 0);
+    B = __shfl_sync(kFullMask, p, 1);
+    C = __shfl_sync(kFullMask, p, 2);
   } else {
     const double th = sqrt(th2);
-    double s, c;
-    sincos(th, &s, &c);
-    A = s / th;
-    B = (1.0 - c) / th2;
-    C = (th - s) / (th2 * th);
+    double sn, cs;
+    sincos(th, &sn, &cs);
+    A = sn / th;
+    B = (1.0 - cs) / th2;
+    C = (th - sn) / (th2 * th);
   }
-  const double K[3][3] = {{0.0, -wz, wy}, {wz, 0.0, -wx}, {-wy, wx, 0.0}};
-  double K2[3][3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) K2[i][j] = K[i][0] * K[0][j] + K[i][1] * K[1][j] + K[i][2] * K[2][j];
-  double Ri[3][3], V[3][3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      const double I = (i == j) ? 1.0 : 0.0;
-      Ri[i][j] = I + A * K[i][j] + B * K2[i][j];
-      V[i][j] = I + B * K[i][j] + C * K2[i][j];
-    }
-  double Tn[12];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-#pragma unroll
-    for (int j = 0; j < 3; ++j)
-      Tn[i * 4 + j] = Ri[i][0] * T[0 * 4 + j] + Ri[i][1] * T[1 * 4 + j] + Ri[i][2] * T[2 * 4 + j];
-    Tn[i * 4 + 3] = Ri[i][0] * T[3] + Ri[i][1] * T[7] + Ri[i][2] * T[11] +
-                    (V[i][0] * xi[3] + V[i][1] * xi[4] + V[i][2] * xi[5]);
+  const bool rot = lane < 12;
+  const int r = rot ? lane >> 2 : (lane < 15 ? lane - 12 : 0), c = lane & 3;
+  const double al = rot ? A : B, be = rot ? B : C;
+  const double wr = pick3(r, wx, wy, wz);
+  // row r of K: (0, -wz, wy), (wz, 0, -wx), (-wy, wx, 0)
+  const double k0 = pick3(r, 0.0, wz, -wy), k1 = pick3(r, -wz, 0.0, wx), k2 = pick3(r, wy, -wx, 0.0);
+  const double q0 = fma(wr, wx, r == 0 ? -th2 : 0.0);
+  const double q1 = fma(wr, wy, r == 1 ? -th2 : 0.0);
+  const double q2 = fma(wr, wz, r == 2 ? -th2 : 0.0);
+  const double M0 = fma(al, k0, fma(be, q0, r == 0 ? 1.0 : 0.0));
+  const double M1 = fma(al, k1, fma(be, q1, r == 1 ? 1.0 : 0.0));
+  const double M2 = fma(al, k2, fma(be, q2, r == 2 ? 1.0 : 0.0));
+  const double y0 = rot ? T[c] : xi[3], y1 = rot ? T[4 + c] : xi[4], y2 = rot ? T[8 + c] : xi[5];
+  double acc = fma(M2, y2, fma(M1, y1, M0 * y0));
+  const double vt = __shfl_sync(kFullMask, acc, 12 + r);
+  if (rot && c == 3) acc += vt;
+  __syncwarp();
+  if (rot) {
+    T[lane] = acc;
+    if (Tf) Tf[lane] = (float)acc;
   }
-#pragma unroll
-  for (int k = 0; k < 12; ++k) T[k] = Tn[k];
+  __syncwarp();
 }
 
 }  // namespace
@@ -487,52 +543,47 @@ __global__ void __launch_bounds__(THREADS, RIMG_ICP_THREADS_PER_SM / THREADS) k_
   }
 }
 
-// The Gauss-Newton update from a pair's FP64 sums t[0..28]: FP64
-// Cholesky-type solve of the 6x6 system and T <- Exp(xi) T for the 3x4 pose
-// T; t[29], t[30] receive |omega| (rad) and |tau| (m) of the step and t[31]
-// 1 if it was applied (0: fewer than 6 correspondences or a degenerate pivot,
-// T unchanged).  Returns whether it was applied.
-__device__ bool solve_and_update(double* t, double* T) {
-  double Hm[6][6], g[6], x[6];
-  int q = 0;
-  for (int i = 0; i < 6; ++i)
-    for (int j = i; j < 6; ++j) { Hm[i][j] = t[q]; Hm[j][i] = t[q]; ++q; }
-  for (int i = 0; i < 6; ++i) g[i] = t[21 + i];
+// The Gauss-Newton update from a pair's FP64 sums t[0..28], by all 32 lanes
+// of one warp: FP64 solve of the 6x6 system and T <- Exp(xi) T for the 3x4
+// pose T (Tf: optional FP32 copy of the new pose).  rec, if given, receives
+// |omega| (rad) and |tau| (m) of the step (to FP32 precision) and 1 if it was applied (0, 0, 0:
+// fewer than 6 correspondences or a degenerate pivot, T unchanged).  Returns
+// whether it was applied (the same in every lane).
+__device__ __noinline__ bool warp_gn_update(const double* t, double* T, float* Tf, double* rec, int lane) {
+  double x[6];
   bool good = t[28] >= 6.0;
-  if (good) good = chol6_solve(Hm, g, x);
-  if (good) {
-    se3_left_update(T, x);
-    t[29] = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
-    t[30] = sqrt(x[3] * x[3] + x[4] * x[4] + x[5] * x[5]);
-    t[31] = 1.0;
-  } else {
-    t[29] = 0.0;
-    t[30] = 0.0;
-    t[31] = 0.0;
+  if (good) good = warp_solve6(t, lane, x);
+  if (good) warp_se3_update(T, x, lane, Tf);
+  if (rec && lane < 3) {
+    double val = 0.0;
+    if (good) {
+      if (lane == 2) {
+        val = 1.0;
+      } else {
+        const double p = lane ? x[3] : x[0], q = lane ? x[4] : x[1], r = lane ? x[5] : x[2];
+        val = (double)sqrtf((float)fma(r, r, fma(q, q, p * p)));   // a diagnostic: FP32 root
+      }
+    }
+    rec[lane] = val;
   }
   return good;
 }
 
-// The Gauss-Newton update of every pair from its FP64 sums: one thread per
-// pair.  Kept out of k_icp so that no reduction block holds an SM slot
-// through the serial FP64 chain.  The pair's record keeps the size of the
+// The Gauss-Newton update of every pair from its FP64 sums: one warp per pair
+// (four per block).  Kept out of k_icp so that no reduction block holds an
+// SM slot through the FP64 chain.  The pair's record keeps the size of the
 // step in its spare slots.
-__global__ void __launch_bounds__(32) k_solve(int n_pairs, double* __restrict__ sums,
-                                             double* __restrict__ pose, int* __restrict__ status) {
-  const int pair = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(128) k_solve(int n_pairs, double* sums, double* pose, int* __restrict__ status) {
+  const int pair = blockIdx.x * 4 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
   if (pair >= n_pairs) return;
-  double T[12];
-  double* P = pose + (long long)pair * 16;
-  for (int k = 0; k < 12; ++k) T[k] = P[k];
-  if (solve_and_update(sums + (long long)pair * kRedStride, T)) {
-    for (int k = 0; k < 12; ++k) P[k] = T[k];
-  } else if (status) {
-    status[pair] |= RIMG_FLAG_DEGENERATE;
-  }
+  double* t = sums + (long long)pair * kRedStride;
+  const bool ok = warp_gn_update(t, pose + (long long)pair * 16, nullptr, t + 29, lane);
+  if (!ok && lane == 0 && status) status[pair] |= RIMG_FLAG_DEGENERATE;
 }
 
 // All iterations of one small level in one launch: one block per pair
-// associates and reduces the pair's whole level, its first thread solves in
+// associates and reduces the pair's whole level, its first warp solves in
 // FP64 and updates the pose in shared memory, and the block goes on with the
 // next iteration -- the per-iteration launches (association + solve) of a
 // level whose pair fits one block collapse into one.  Same arithmetic as
@@ -556,9 +607,10 @@ __global__ void __launch_bounds__(THREADS, RIMG_ICP_THREADS_PER_SM / THREADS) k_
     icp_block_terms<R0, GATE, false, KAHAN, THREADS>(a, sm, pair, 0, a.src.H);
     if (tid < kRed) sm.tot[tid] = (double)block_total(sm, tid);
     __syncthreads();
-    if (tid == 0) {
-      if (!solve_and_update(sm.tot, Tp)) degenerate = 1;
-      for (int k = 0; k < 12; ++k) reinterpret_cast<float*>(sm.T4)[k] = (float)Tp[k];
+    if (tid < 32) {
+      const bool ok = warp_gn_update(sm.tot, Tp, reinterpret_cast<float*>(sm.T4), it == iters - 1 ? sm.tot + 29 : nullptr,
+                                     tid);
+      if (!ok && tid == 0) degenerate = 1;
     }
     __syncthreads();
   }
@@ -569,7 +621,7 @@ __global__ void __launch_bounds__(THREADS, RIMG_ICP_THREADS_PER_SM / THREADS) k_
 
 cudaError_t launch_solve(int n_pairs, double* sums, double* pose, int* status, cudaStream_t st) {
   if (n_pairs == 0) return cudaSuccess;
-  k_solve<<<(n_pairs + 31) / 32, 32, 0, st>>>(n_pairs, sums, pose, status);
+  k_solve<<<(n_pairs + 3) / 4, 128, 0, st>>>(n_pairs, sums, pose, status);
   return cudaGetLastError();
 }
 
