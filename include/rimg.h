@@ -175,7 +175,8 @@ int rimg_pyramid(int n_images, int H, int W, int levels, int channels, const flo
  * device pointers) entry l receives float4 [n][H_l][W_l] = (n_x, n_y, n_z, d)
  * with d = n . P, strided from the finest level like rimg_pyramid (normals are
  * strided, not recomputed, Section 4.1).  mask0 (nullable): uint8 [n][H][W],
- * 1 = valid normal at the finest level.
+ * 1 = valid normal at the finest level.  range and every planes_levels[l]:
+ * device, 16-byte aligned (RIMG_ERR_INVALID_ARG otherwise).
  * ------------------------------------------------------------------------- */
 int rimg_normals(const rimg_sensor* s, int n_images, const float* range, const rimg_params* p,
                  float* const* planes_levels, uint8_t* mask0, void* stream);

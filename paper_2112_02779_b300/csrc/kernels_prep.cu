@@ -1,6 +1,8 @@
 // Per-image preprocessing kernels: unprojection (Eq. 1-2), the strided
 // pyramid (Section 4.1) and neighbour-cross-product normals (Section 4.1)
 // with the target plane pyramid written by the same kernel.
+#include <algorithm>
+
 #include "rimg_device.cuh"
 
 namespace rimg {
@@ -90,12 +92,12 @@ cudaError_t launch_pyramid(int n, int H, int W, int levels, int channels, const 
 }
 
 // --------------------------------------------------------------------------
-// Normals.  A 32 x 8 tile of output pixels per block; the block unprojects the
-// (32+2) x (8+2) halo tile into shared memory once (u wraps, rows outside the
-// image are invalid), then each thread forms the two central differences,
-// their cross product and the validity tests, and writes the plane
-// (n, n . P) to level 0 and, when its coordinates are multiples of 2^l, to
-// level l (the strided normal pyramid).
+// Normals.  Both kernels unproject a halo tile of the target image into
+// shared memory once (u wraps around the 360 degree image, rows outside the
+// image are invalid), form each pixel's normal from its neighbours there and
+// write the plane (n, n . P) to level 0 and, when the pixel's coordinates are
+// multiples of 2^l, to level l (the strided normal pyramid).  PCA variant: a
+// 32 x 8 tile, one pixel per thread.
 constexpr int NT_X = 32, NT_Y = 8;
 constexpr int NH_X = NT_X + 2, NH_Y = NT_Y + 2;
 
@@ -189,10 +191,8 @@ __device__ __forceinline__ bool pca_normal(const float (&q)[9][3], const bool (&
   return true;
 }
 
-template <bool PCA>
-__global__ void __launch_bounds__(NT_X* NT_Y) k_normals(DevLevel L, int levels, int n, const float* __restrict__ range,
-                                                        float rel_jump, PlaneOut out,
-                                                        uint8_t* __restrict__ mask0) {
+__global__ void __launch_bounds__(NT_X* NT_Y) k_normals_pca(DevLevel L, int levels, const float* __restrict__ range,
+                                                            float rel_jump, PlaneOut out, uint8_t* __restrict__ mask0) {
   __shared__ float4 sp[NH_Y][NH_X];   // point (x, y, z) and range (0: invalid) of each tile pixel
   const int img = blockIdx.z;
   const int u0 = blockIdx.x * NT_X - 1, v0 = blockIdx.y * NT_Y - 1;
@@ -236,71 +236,217 @@ __global__ void __launch_bounds__(NT_X* NT_Y) k_normals(DevLevel L, int levels, 
   const int cx = threadIdx.x + 1, cy = threadIdx.y + 1;
   const float4 C = sp[cy][cx];
   const float rc = C.w;
-  if (PCA) {
-    float q[9][3];
-    bool use[9];
-    const float px = C.x, py = C.y, pz = C.z;
+  float q[9][3];
+  bool use[9];
+  const float px = C.x, py = C.y, pz = C.z;
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      const float4 Q = sp[cy + i / 3 - 1][cx + i % 3 - 1];
-      use[i] = rc > 0.f && Q.w > 0.f && fmaf(rel_jump, rc, -fabsf(Q.w - rc)) >= 0.f;
-      q[i][0] = Q.x - px;
-      q[i][1] = Q.y - py;
-      q[i][2] = Q.z - pz;
-    }
-    float nx = 0.f, ny = 0.f, nz = 0.f;
-    bool ok = (v > 0) && (v < H - 1) && rc > 0.f && pca_normal(q, use, nx, ny, nz);
-    float4 plane = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (ok) {
-      float d = fmaf(nx, px, fmaf(ny, py, nz * pz));
-      if (d > 0.f) { nx = -nx; ny = -ny; nz = -nz; d = -d; }
-      plane = make_float4(nx, ny, nz, d);
-    }
-    write_plane(out, mask0, img, H, W, u, v, levels, plane, ok);
-    return;
+  for (int i = 0; i < 9; ++i) {
+    const float4 Q = sp[cy + i / 3 - 1][cx + i % 3 - 1];
+    use[i] = rc > 0.f && Q.w > 0.f && fmaf(rel_jump, rc, -fabsf(Q.w - rc)) >= 0.f;
+    q[i][0] = Q.x - px;
+    q[i][1] = Q.y - py;
+    q[i][2] = Q.z - pz;
   }
-  const float4 Pl = sp[cy][cx - 1], Pr = sp[cy][cx + 1], Pu = sp[cy - 1][cx], Pd = sp[cy + 1][cx];
-  const float rl = Pl.w, rr = Pr.w, ru = Pu.w, rd = Pd.w;
-  // |r_nb - r_c| <= rel_jump * r_c decided exactly: the difference is exact
-  // (Sterbenz) whenever the test can pass, and the sign of one fused
-  // multiply-add is the sign of the exact value.
-  bool ok = (v > 0) && (v < H - 1) && rc > 0.f && rl > 0.f && rr > 0.f && ru > 0.f && rd > 0.f;
-  ok = ok && fmaf(rel_jump, rc, -fabsf(rl - rc)) >= 0.f && fmaf(rel_jump, rc, -fabsf(rr - rc)) >= 0.f &&
-       fmaf(rel_jump, rc, -fabsf(ru - rc)) >= 0.f && fmaf(rel_jump, rc, -fabsf(rd - rc)) >= 0.f;
-  const float ax = Pr.x - Pl.x, ay = Pr.y - Pl.y, az = Pr.z - Pl.z;
-  const float bx = Pd.x - Pu.x, by = Pd.y - Pu.y, bz = Pd.z - Pu.z;
-  float nx = fmaf(ay, bz, -az * by), ny = fmaf(az, bx, -ax * bz), nz = fmaf(ax, by, -ay * bx);
-  const float c2 = fmaf(nx, nx, fmaf(ny, ny, nz * nz));
-  const float a2 = fmaf(ax, ax, fmaf(ay, ay, az * az));
-  const float b2 = fmaf(bx, bx, fmaf(by, by, bz * bz));
-  ok = ok && (c2 > 1e-8f * a2 * b2);
+  float nx = 0.f, ny = 0.f, nz = 0.f;
+  bool ok = (v > 0) && (v < H - 1) && rc > 0.f && pca_normal(q, use, nx, ny, nz);
   float4 plane = make_float4(0.f, 0.f, 0.f, 0.f);
   if (ok) {
-    const float inv = rsqrtf(c2);
-    nx *= inv; ny *= inv; nz *= inv;
-    float d = fmaf(nx, C.x, fmaf(ny, C.y, nz * C.z));
+    float d = fmaf(nx, px, fmaf(ny, py, nz * pz));
     if (d > 0.f) { nx = -nx; ny = -ny; nz = -nz; d = -d; }
     plane = make_float4(nx, ny, nz, d);
   }
   write_plane(out, mask0, img, H, W, u, v, levels, plane, ok);
 }
 
+// Cross-product normals, one warp per strip of 128 columns x NC_ROWS rows and
+// four horizontally adjacent pixels per lane.  The warp walks down its strip
+// with a rolling window of three unprojected rows held in registers (rows
+// v - 1, v, v + 1), so every range row is loaded and unprojected once per
+// strip, with the range loads issued two rows ahead of their use.  The left
+// and right neighbours of a lane's group come from the adjacent lanes by
+// shuffle; the strip's two edge columns are loaded by lanes 0 and 31.
+// Columns wrap around the 360 degree image (W is a multiple of 4, so a group
+// never straddles the wrap, and a lane past the image's last column holds
+// the wrapped columns that the last active lane needs).  No shared memory
+// and no barriers.  Per pixel the arithmetic is that of the one-pixel form
+// (the same operations in the same order).
+constexpr int NC_LANES_PX = 4;
+constexpr int NC_W = 32 * NC_LANES_PX;   // strip width in pixels
+constexpr int NC_ROWS = 16;              // output rows per strip
+constexpr int NC_WARPS = 4;              // warps per block
+
+// Unprojection (Eq. 1-2) of one pixel from its row entry and column cos/sin;
+// all zero when the pixel is invalid (rows outside the image arrive as range 0).
+__device__ __forceinline__ float4 stage_point(const float4& rw, float cu, float su, float r0, float rq) {
+  const bool ok = range_ok(rq);
+  const float ct = fmaf(cu, rw.z, -su * rw.w);
+  const float st = fmaf(su, rw.z, cu * rw.w);
+  const float rc = rq * rw.x;
+  return ok ? make_float4(fmaf(rc, ct, r0 * cu), fmaf(rc, st, r0 * su), rq * rw.y, rq)
+            : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+__device__ __forceinline__ float4 shfl4(const float4& a, int src) {
+  return make_float4(__shfl_sync(0xffffffffu, a.x, src), __shfl_sync(0xffffffffu, a.y, src),
+                     __shfl_sync(0xffffffffu, a.z, src), __shfl_sync(0xffffffffu, a.w, src));
+}
+
+struct Row4 {
+  float4 p[4];   // x, y, z, range of the lane's four pixels
+};
+
+__global__ void __launch_bounds__(32 * NC_WARPS) k_normals_cross(DevLevel L, int levels, int n_img,
+                                                                 const float* __restrict__ range, float rel_jump,
+                                                                 PlaneOut out, uint8_t* __restrict__ mask0) {
+  const int H = L.H, W = L.W;
+  const long long N = (long long)H * W;
+  const int lane = threadIdx.x & 31;
+  const int segs = (W + NC_W - 1) / NC_W;
+  const int per_img = segs * ((H + NC_ROWS - 1) / NC_ROWS);
+  // strip index: < 2^31 for every accepted size (the launcher caps the images per launch)
+  const int strip = blockIdx.x * NC_WARPS + (threadIdx.x >> 5);
+  if (strip >= per_img * n_img) return;   // whole warps only
+  const int img = strip / per_img;
+  const int rem = strip - img * per_img;
+  const int rb = rem / segs;
+  const int c0 = (rem - rb * segs) * NC_W, v0 = rb * NC_ROWS;
+  auto wrap = [&](int u) {
+    if (u < 0) u += W;
+    if (u >= W) u = (W >= NC_W) ? u - W : u % W;
+    return u;
+  };
+  const float* rimg = range + img * N;
+  const int u0 = c0 + NC_LANES_PX * lane;
+  const int g = wrap(u0);
+  const float4 cu = __ldg(reinterpret_cast<const float4*>(L.cos_u + g));
+  const float4 su = __ldg(reinterpret_cast<const float4*>(L.sin_u + g));
+  const bool edge = lane == 0 || lane == 31;
+  const int ue = wrap(lane == 0 ? c0 - 1 : c0 + NC_W);   // the edge lanes' extra column
+  const float cue = __ldg(L.cos_u + ue), sue = __ldg(L.sin_u + ue);
+  auto load_row = [&](int vv) {
+    return (vv >= 0 && vv < H) ? __ldg(reinterpret_cast<const float4*>(rimg + (long long)vv * W + g))
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
+  };
+  auto load_edge = [&](int vv) { return (edge && vv >= 0 && vv < H) ? __ldg(rimg + (long long)vv * W + ue) : 0.f; };
+  auto row_entry = [&](int vv) { return __ldg(L.rows + min(max(vv, 0), H - 1)); };
+  auto unproject_row = [&](int vv, const float4& r4) {
+    const float4 rw = row_entry(vv);
+    Row4 R;
+    R.p[0] = stage_point(rw, cu.x, su.x, L.r0, r4.x);
+    R.p[1] = stage_point(rw, cu.y, su.y, L.r0, r4.y);
+    R.p[2] = stage_point(rw, cu.z, su.z, L.r0, r4.z);
+    R.p[3] = stage_point(rw, cu.w, su.w, L.r0, r4.w);
+    return R;
+  };
+  const bool col_ok = u0 < W;
+  const bool mask_aligned = (reinterpret_cast<uintptr_t>(mask0) & 3) == 0;
+
+  Row4 Pu = unproject_row(v0 - 1, load_row(v0 - 1));
+  Row4 Pc = unproject_row(v0, load_row(v0));
+  float4 r_next = load_row(v0 + 1);          // range of row v + 1
+  float4 r_next2 = load_row(v0 + 2);         // range of row v + 2
+  float e_cur = load_edge(v0);               // edge range of row v
+#pragma unroll
+  for (int i = 0; i < NC_ROWS; ++i) {
+    const int v = v0 + i;
+    const Row4 Pd = unproject_row(v + 1, r_next);
+    r_next = r_next2;
+    r_next2 = load_row(v + 3);
+    const float e_next = load_edge(v + 1);
+    // left neighbour of pixel 0 and right neighbour of pixel 3 in row v
+    float4 Pl = shfl4(Pc.p[3], (lane + 31) & 31);
+    float4 Pr = shfl4(Pc.p[0], (lane + 1) & 31);
+    if (edge) {
+      const float4 p = stage_point(row_entry(v), cue, sue, L.r0, e_cur);
+      if (lane == 0) Pl = p; else Pr = p;
+    }
+    if (v < H && col_ok) {
+      const bool row_ok = (v > 0) && (v < H - 1);
+      float4 plane[4];
+      bool okq[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float4 C = Pc.p[q];
+        const float4 A = q == 0 ? Pl : Pc.p[q - 1];
+        const float4 B = q == 3 ? Pr : Pc.p[q + 1];
+        const float4 Up = Pu.p[q], Dn = Pd.p[q];
+        const float rc = C.w, rl = A.w, rr = B.w, ru = Up.w, rd = Dn.w;
+        bool ok = row_ok && rc > 0.f && rl > 0.f && rr > 0.f && ru > 0.f && rd > 0.f;
+        ok = ok && fmaf(rel_jump, rc, -fabsf(rl - rc)) >= 0.f && fmaf(rel_jump, rc, -fabsf(rr - rc)) >= 0.f &&
+             fmaf(rel_jump, rc, -fabsf(ru - rc)) >= 0.f && fmaf(rel_jump, rc, -fabsf(rd - rc)) >= 0.f;
+        const float ax = B.x - A.x, ay = B.y - A.y, az = B.z - A.z;
+        const float bx = Dn.x - Up.x, by = Dn.y - Up.y, bz = Dn.z - Up.z;
+        float nx = fmaf(ay, bz, -az * by), ny = fmaf(az, bx, -ax * bz), nz = fmaf(ax, by, -ay * bx);
+        const float c2 = fmaf(nx, nx, fmaf(ny, ny, nz * nz));
+        const float a2 = fmaf(ax, ax, fmaf(ay, ay, az * az));
+        const float b2 = fmaf(bx, bx, fmaf(by, by, bz * bz));
+        ok = ok && (c2 > 1e-8f * a2 * b2);
+        float4 pl = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (ok) {
+          const float inv = rsqrtf(c2);
+          nx *= inv; ny *= inv; nz *= inv;
+          float d = fmaf(nx, C.x, fmaf(ny, C.y, nz * C.z));
+          if (d > 0.f) { nx = -nx; ny = -ny; nz = -nz; d = -d; }
+          pl = make_float4(nx, ny, nz, d);
+        }
+        plane[q] = pl;
+        okq[q] = ok;
+      }
+      const long long o0 = img * N + (long long)v * W + u0;
+      float4* p0 = out.p[0] + o0;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) p0[q] = plane[q];
+      if (mask0) {
+        const uchar4 m = make_uchar4(okq[0], okq[1], okq[2], okq[3]);
+        if (mask_aligned) {
+          *reinterpret_cast<uchar4*>(mask0 + o0) = m;
+        } else {
+          mask0[o0] = m.x; mask0[o0 + 1] = m.y; mask0[o0 + 2] = m.z; mask0[o0 + 3] = m.w;
+        }
+      }
+      // the strided pyramid: level 1 takes pixels 0 and 2 of the group on
+      // even rows, level l >= 2 pixel 0 where u0 and v are multiples of 2^l
+      if (levels > 1 && (v & 1) == 0) {
+        const int W1 = W >> 1;
+        float4* p1 = out.p[1] + img * (long long)(H >> 1) * W1 + (long long)(v >> 1) * W1 + (u0 >> 1);
+        p1[0] = plane[0];
+        p1[1] = plane[2];
+#pragma unroll
+        for (int l = 2; l < RIMG_MAX_LEVELS; ++l) {
+          const int m = (1 << l) - 1;
+          if (l >= levels || ((u0 & m) | (v & m))) break;
+          const int Hl = H >> l, Wl = W >> l;
+          out.p[l][img * (long long)Hl * Wl + (long long)(v >> l) * Wl + (u0 >> l)] = plane[0];
+        }
+      }
+    }
+    Pu = Pc;
+    Pc = Pd;
+    e_cur = e_next;
+  }
+}
+
 cudaError_t launch_normals(const rimg_sensor* s, int n, const float* range, float rel_jump, int method,
                            float* const* planes_levels, uint8_t* mask0, cudaStream_t st) {
   const DevLevel L = dev_level(s, 0);
   const long long N = (long long)L.H * L.W;
-  for (int off = 0; off < n; off += 65535) {       // grid.z limit
-    const int cnt = n - off < 65535 ? n - off : 65535;
+  // images per launch: the PCA grid's z limit; for the strip kernel, strip
+  // indices below 2^31
+  const long long per_img = (long long)((L.W + NC_W - 1) / NC_W) * ((L.H + NC_ROWS - 1) / NC_ROWS);
+  const int chunk = (method == 1) ? 65535 : (int)std::max(1LL, std::min(65535LL, 2147483647LL / per_img));
+  for (int off = 0; off < n; off += chunk) {
+    const int cnt = n - off < chunk ? n - off : chunk;
     PlaneOut o{};
     for (int l = 0; l < s->levels; ++l)
       o.p[l] = reinterpret_cast<float4*>(planes_levels[l]) + (long long)off * (L.H >> l) * (L.W >> l);
-    dim3 grid((L.W + NT_X - 1) / NT_X, (L.H + NT_Y - 1) / NT_Y, cnt);
-    if (method == 1)
-      k_normals<true><<<grid, dim3(NT_X, NT_Y), 0, st>>>(L, s->levels, cnt, range + off * N, rel_jump, o,
-                                                         mask0 ? mask0 + off * N : nullptr);
-    else
-      k_normals<false><<<grid, dim3(NT_X, NT_Y), 0, st>>>(L, s->levels, cnt, range + off * N, rel_jump, o,
-                                                          mask0 ? mask0 + off * N : nullptr);
+    uint8_t* m = mask0 ? mask0 + off * N : nullptr;
+    if (method == 1) {
+      dim3 grid((L.W + NT_X - 1) / NT_X, (L.H + NT_Y - 1) / NT_Y, cnt);
+      k_normals_pca<<<grid, dim3(NT_X, NT_Y), 0, st>>>(L, s->levels, range + off * N, rel_jump, o, m);
+    } else {
+      const unsigned blocks = (unsigned)((per_img * cnt + NC_WARPS - 1) / NC_WARPS);
+      k_normals_cross<<<blocks, 32 * NC_WARPS, 0, st>>>(L, s->levels, cnt, range + off * N, rel_jump, o, m);
+    }
   }
   return cudaGetLastError();
 }

@@ -763,9 +763,9 @@ int rimg_normals(const rimg_sensor* s, int n_images, const float* range, const r
   if ((rc = check_params(p))) return rc;
   if (n_images < 0) return RIMG_ERR_INVALID_ARG;
   if (n_images == 0) return RIMG_OK;
-  if (!range || !planes_levels) return RIMG_ERR_INVALID_ARG;
+  if (!range || !planes_levels || (reinterpret_cast<uintptr_t>(range) % 16)) return RIMG_ERR_INVALID_ARG;
   for (int l = 0; l < s->levels; ++l)
-    if (!planes_levels[l]) return RIMG_ERR_INVALID_ARG;
+    if (!planes_levels[l] || (reinterpret_cast<uintptr_t>(planes_levels[l]) % 16)) return RIMG_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   prof_before(st, K_NORMALS, 0, n_images);
   cudaError_t e = launch_normals(s, n_images, range, p->normal_rel_jump, p->normal_method, planes_levels, mask0, st);

@@ -123,6 +123,25 @@ def test_entry_points_reject_null_and_bad_arguments():
     assert lib.rimg_profile_begin(-1) == -1
 
 
+def test_normals_entry_point_rejects_misaligned_buffers_on_the_host():
+    """rimg_normals reads ranges and writes planes 16 bytes at a time: a
+    range or plane pointer off a 16-byte boundary is refused before any launch."""
+    lib = R.lib()
+    s = _abi.rimg_sensor()
+    fake = 1 << 20                                    # never dereferenced: the checks come first
+    s.d_tables = fake
+    s.H, s.W, s.levels = 16, 64, 2
+    s.level[0].H, s.level[0].W = 16, 64
+    s.level[1].H, s.level[1].W = 8, 32
+    p = R.rimg_default_params()
+    vp = ctypes.c_void_p
+    good = (vp * _abi.RIMG_MAX_LEVELS)(fake, fake + 4096)
+    assert lib.rimg_normals(ctypes.byref(s), 1, fake + 4, ctypes.byref(p), good, None, None) == -1
+    bad = (vp * _abi.RIMG_MAX_LEVELS)(fake, fake + 4104)
+    assert lib.rimg_normals(ctypes.byref(s), 1, fake, ctypes.byref(p), bad, None, None) == -1
+    assert lib.rimg_normals(ctypes.byref(s), 0, fake + 4, ctypes.byref(p), good, None, None) == 0   # no-op
+
+
 def test_cnn_entry_points_check_arguments_on_the_host():
     lib = R.lib()
     n = ctypes.c_size_t()
