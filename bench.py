@@ -473,8 +473,8 @@ def run_ours(args):
                      "in_step": {"achieved": in_step, "frac": in_step / peak, "launches": len(l0),
                                  "busy_ms": l0_union,
                                  "how": "level-0 k_icp bytes of the timed steps over the union of their launch "
-                                        "intervals (CUDA events around each launch, timed region 2); the two "
-                                        "sub-batch streams' other kernels run concurrently"}},
+                                        "intervals (CUDA events around each launch, timed region 2); the other "
+                                        "sub-batch streams' kernels run concurrently"}},
         "kernels": kernels,
         "profiled_ms_per_step": ms_profiled / args.steps,
         "e2e": e2e,
