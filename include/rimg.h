@@ -221,6 +221,25 @@ int rimg_icp_step(const rimg_sensor* src, const rimg_sensor* dst, int level, int
                   int* status, void* workspace, size_t workspace_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * The Gauss-Newton update alone (step A8), Section 4.1: for each pair, solve
+ * the normal equations of Eq. 7, H xi = -g, in FP64 (LDL^T; not applied when
+ * a pivot is <= 1e-12 trace(H) or with fewer than 6 correspondences) and
+ * apply T <- Exp(xi) T, xi = (omega, tau).  It is the update rimg_icp_step
+ * applies with update = 1, for sums that the caller combined itself (for
+ * instance the out29 records of partial images or of several devices, added).
+ *
+ * sums: float64 [n_pairs][32] device, 8-byte aligned, in place.  Entries
+ * 0..28 are read: the 29 reduced quantities in out29's order (21 upper-
+ * triangle entries of J^T W J row-major, 6 of J^T W e, sum w e^2, count).
+ * Entries 29..31 are written: |omega| (rad) and |tau| (m) of the step, to
+ * FP32 precision, and 1 if it was applied (0, 0, 0 otherwise).
+ * pose: float64 [n_pairs][16] device, row-major 4x4, updated in place
+ * (unchanged when the update is not applied).  status (nullable): int32
+ * [n_pairs] device; RIMG_FLAG_DEGENERATE is OR-ed in when it is not applied.
+ * ------------------------------------------------------------------------- */
+int rimg_gn_update(int n_pairs, double* sums, double* pose, int* status, void* stream);
+
+/* ---------------------------------------------------------------------------
  * rimg_icp_step without a caller workspace.  The paper has no counterpart:
  * this is a library convenience for callers that cannot allocate device
  * memory when they run the step (allocation-free real-time loops, plug-ins

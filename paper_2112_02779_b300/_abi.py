@@ -43,7 +43,7 @@ class rimg_group(ctypes.Structure):
 HEADER_FUNCTIONS = [
     "rimg_default_params", "rimg_status_string", "rimg_last_error",
     "rimg_sensor_table_bytes", "rimg_sensor_build", "rimg_unproject", "rimg_pyramid", "rimg_normals",
-    "rimg_icp_workspace_bytes", "rimg_icp_step", "rimg_icp_step_static",
+    "rimg_icp_workspace_bytes", "rimg_icp_step", "rimg_icp_step_static", "rimg_gn_update",
     "rimg_register_workspace_bytes", "rimg_register", "rimg_register_last_sums",
     "rimg_register_groups_workspace_bytes", "rimg_register_groups", "rimg_autotune", "rimg_autotune_clear",
     "rimg_register_host_workspace_bytes", "rimg_register_host", "rimg_register_host_async",

@@ -808,6 +808,21 @@ int rimg_icp_step(const rimg_sensor* src, const rimg_sensor* dst, int level, int
                     out29, assoc, status, icp_scratch(ws, w, src->H, 0), st);
 }
 
+int rimg_gn_update(int n_pairs, double* sums, double* pose, int* status, void* stream) {
+  if (n_pairs < 0) return RIMG_ERR_INVALID_ARG;
+  if (n_pairs == 0) return RIMG_OK;
+  if (!sums || !pose) return RIMG_ERR_INVALID_ARG;
+  if ((reinterpret_cast<uintptr_t>(sums) % 8) || (reinterpret_cast<uintptr_t>(pose) % 8) ||
+      (reinterpret_cast<uintptr_t>(status) % 4))
+    return RIMG_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  prof_before(st, K_SOLVE, 0, n_pairs);
+  cudaError_t e = launch_solve(n_pairs, sums, pose, status, st);
+  prof_after(st);
+  if (e != cudaSuccess) return cuda_fail(e, "solve kernel");
+  return RIMG_OK;
+}
+
 int rimg_register_workspace_bytes(const rimg_sensor* src, const rimg_sensor* dst, int n_pairs, int levels,
                                   size_t* bytes) {
   if (!bytes) return RIMG_ERR_INVALID_ARG;

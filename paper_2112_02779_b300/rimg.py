@@ -49,6 +49,7 @@ _sig("rimg_icp_step", _c_int, _P(rimg_sensor), _P(rimg_sensor), _c_int, _c_int, 
      _P(rimg_params), _c_int, _vp, _vp, _vp, _vp, _c_size, _vp)
 _sig("rimg_icp_step_static", _c_int, _P(rimg_sensor), _P(rimg_sensor), _c_int, _c_int, _vp, _vp, _vp, _vp,
      _P(rimg_params), _c_int, _vp, _vp, _vp, _vp)
+_sig("rimg_gn_update", _c_int, _c_int, _vp, _vp, _vp, _vp)
 _sig("rimg_register_workspace_bytes", _c_int, _P(rimg_sensor), _P(rimg_sensor), _c_int, _c_int, _P(_c_size))
 _sig("rimg_register", _c_int, _P(rimg_sensor), _P(rimg_sensor), _c_int, _vp, _vp, _vp, _vp, _c_int,
      _P(_c_int), _P(rimg_params), _vp, _vp, _c_size, _vp)
@@ -211,6 +212,12 @@ def rimg_icp_step(src, dst, level, n_pairs, src_range_l, dst_planes_l, dst_range
         src.ref(), dst.ref(), level, n_pairs, _ptr(src_range_l), _ptr(dst_planes_l), _ptr(dst_range_l),
         _ptr(pose), ctypes.byref(params), int(update), _ptr(out29), _ptr(assoc), _ptr(status),
         _ptr(workspace), workspace.numel() if workspace is not None else 0, _stream(stream)))
+
+
+def rimg_gn_update(n_pairs, sums, pose, status=None, stream=None):
+    """The Gauss-Newton update alone: sums float64 [n][32] (0..28 read, 29..31
+    written), pose float64 [n][16], both device tensors, updated in place."""
+    _check("rimg_gn_update", _lib.rimg_gn_update(n_pairs, _ptr(sums), _ptr(pose), _ptr(status), _stream(stream)))
 
 
 def rimg_icp_step_static(src, dst, level, n_pairs, src_range_l, dst_planes_l, dst_range_l, pose, params, update,

@@ -121,6 +121,11 @@ def test_entry_points_reject_null_and_bad_arguments():
     bad = R.rimg_default_params(normal_rel_jump=0.7)
     assert lib.rimg_normals(None, 1, None, ctypes.byref(bad), None, None, None) == -1
     assert lib.rimg_profile_begin(-1) == -1
+    fake = 1 << 20                                    # never dereferenced: the checks come first
+    assert lib.rimg_gn_update(-1, fake, fake, None, None) == -1
+    assert lib.rimg_gn_update(0, None, None, None, None) == 0     # no pairs: no-op
+    assert lib.rimg_gn_update(1, None, fake, None, None) == -1
+    assert lib.rimg_gn_update(1, fake + 4, fake, None, None) == -1   # sums not 8-byte aligned
 
 
 def test_normals_entry_point_rejects_misaligned_buffers_on_the_host():
