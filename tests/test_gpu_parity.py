@@ -92,13 +92,8 @@ def _normal_tolerance(P, ok):
     return np.where(ok, rel + 1e-6, np.inf), pn
 
 
-@pytest.mark.parametrize("name,levels", CFG_LEVELS)
-def test_normals_parity(R, name, levels):
-    cfg = CONFIGS[name]
-    s = cfg.sensor()
-    sens = gpu_sensor(R, s, levels)
+def _check_normals(R, s, sens, imgs, levels):
     params = R.rimg_default_params()
-    imgs = np.stack([make_pair(cfg, i)["dst_range"] for i in range(2)])
     planes, mask = planes_for(R, torch, sens, torch.from_numpy(imgs).cuda(), params)
     for i in range(imgs.shape[0]):
         n_o, ok_o, margin = O.normals(imgs[i], s.phi_lut, s.theta_lut, s.r0, f32(0.1), return_margin=True)
@@ -126,6 +121,34 @@ def test_normals_parity(R, name, levels):
         for l in range(1, levels):
             st = 1 << l
             assert np.array_equal(planes[l][i].cpu().numpy(), pl[::st, ::st])
+    return mask
+
+
+@pytest.mark.parametrize("name,levels", CFG_LEVELS)
+def test_normals_parity(R, name, levels):
+    cfg = CONFIGS[name]
+    s = cfg.sensor()
+    sens = gpu_sensor(R, s, levels)
+    imgs = np.stack([make_pair(cfg, i)["dst_range"] for i in range(2)])
+    _check_normals(R, s, sens, imgs, levels)
+
+
+@pytest.mark.parametrize("H,W,levels", [(8, 136, 1), (12, 64, 2), (24, 1152, 3), (16, 4, 1)])
+def test_normals_parity_strip_edges(R, H, W, levels):
+    """Widths that end inside a 128-column strip (136, 64, 4: the wrap lands in
+    a lane of the same warp), a width of nine strips, and heights that end
+    inside a 16-row strip."""
+    from synth import Sensor, outdoor_scene, raycast, uniform_phi
+    rng = np.random.default_rng(H * 1000 + W)
+    s = Sensor(H, W, uniform_phi(H, 8.0, -20.0), rng.uniform(-0.01, 0.01, H), 0.04)
+    scene = outdoor_scene(rng, 60, 40.0)
+    Wd = np.eye(4)
+    Wd[2, 3] = 1.7
+    imgs = np.stack([raycast(scene, s, Wd, 1.0, 60.0, 0.01, 0.05, rng) for _ in range(2)]).astype(np.float32)
+    sens = gpu_sensor(R, s, levels)
+    mask = _check_normals(R, s, sens, imgs, levels)
+    if W >= 64:
+        assert mask.sum().item() > 0.1 * imgs.size
 
 
 # ---------------------------------------------------------------------------
