@@ -376,19 +376,28 @@ __device__ __forceinline__ void icp_block_terms(const IcpLaunch& a, IcpSmem<THRE
     const float4 ss4 = __ldg(reinterpret_cast<const float4*>(S.sin_u + u0));
     const float cs[4] = {cc4.x, cc4.y, cc4.z, cc4.w}, sn[4] = {ss4.x, ss4.y, ss4.z, ss4.w};
     const float4 T0 = sm.T4[0], T1 = sm.T4[1], T2 = sm.T4[2];
+    // Unprojection and transform folded: with the row's cos/sin(phi) and
+    // cos/sin(theta_lut) and the rotation columns R0, R1, R2,
+    //   R p = r (cs A + sn B + C),  A = cos(phi) (cos(th) R0 + sin(th) R1),
+    //   B = cos(phi) (cos(th) R1 - sin(th) R0),  C = sin(phi) R2,
+    // plus r0 (cs R0 + sn R1) with a receiver offset.
+    const float q0 = rw.x * rw.z, q1 = rw.x * rw.w;
+    const float3 A = make_float3(fmaf(q0, T0.x, q1 * T0.y), fmaf(q0, T1.x, q1 * T1.y), fmaf(q0, T2.x, q1 * T2.y));
+    const float3 B = make_float3(fmaf(q0, T0.y, -q1 * T0.x), fmaf(q0, T1.y, -q1 * T1.x), fmaf(q0, T2.y, -q1 * T2.x));
+    const float3 C = make_float3(rw.y * T0.z, rw.y * T1.z, rw.y * T2.z);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const bool valid = range_ok(rr[q]);
       const float r = valid ? rr[q] : 0.f;
-      const float ct = fmaf(cs[q], rw.z, -sn[q] * rw.w);
-      const float st = fmaf(sn[q], rw.z, cs[q] * rw.w);
-      const float rc = r * rw.x;
-      const float px = R0 ? fmaf(rc, ct, S.r0 * cs[q]) : rc * ct;
-      const float py = R0 ? fmaf(rc, st, S.r0 * sn[q]) : rc * st;
-      const float pz = r * rw.y;
-      const float X = fmaf(T0.x, px, fmaf(T0.y, py, fmaf(T0.z, pz, T0.w)));
-      const float Y = fmaf(T1.x, px, fmaf(T1.y, py, fmaf(T1.z, pz, T1.w)));
-      const float Z = fmaf(T2.x, px, fmaf(T2.y, py, fmaf(T2.z, pz, T2.w)));
+      const float Dx = fmaf(cs[q], A.x, fmaf(sn[q], B.x, C.x));
+      const float Dy = fmaf(cs[q], A.y, fmaf(sn[q], B.y, C.y));
+      const float Dz = fmaf(cs[q], A.z, fmaf(sn[q], B.z, C.z));
+      const float ox = R0 ? fmaf(S.r0 * cs[q], T0.x, fmaf(S.r0 * sn[q], T0.y, T0.w)) : T0.w;
+      const float oy = R0 ? fmaf(S.r0 * cs[q], T1.x, fmaf(S.r0 * sn[q], T1.y, T1.w)) : T1.w;
+      const float oz = R0 ? fmaf(S.r0 * cs[q], T2.x, fmaf(S.r0 * sn[q], T2.y, T2.w)) : T2.w;
+      const float X = fmaf(r, Dx, ox);
+      const float Y = fmaf(r, Dy, oy);
+      const float Z = fmaf(r, Dz, oz);
       int uu, vv;
       const bool fov = project_px<R0>(D, make_float3(X, Y, Z), a.proj_iters, uu, vv);
       const bool ok = valid && fov;
