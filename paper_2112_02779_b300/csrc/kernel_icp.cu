@@ -246,7 +246,9 @@ __device__ __forceinline__ void accumulate_px(float2 (&t)[kPairs], float x, floa
   t[11] = fma2(U01, E2, t[11]);                        // g0 g1
   t[12] = fma2(U23, E2, t[12]);                        // g2 g3
   t[13] = fma2(U45, E2, t[13]);                        // g4 g5
-  t[14].x += (nx != 0.f || ny != 0.f || nz != 0.f) ? 1.f : 0.f;
+  // an association counts when its plane is not the all-zero invalid plane
+  // (stored as +0.f; a unit normal has a non-zero component)
+  t[14].x += (__float_as_uint(nx) | __float_as_uint(ny) | __float_as_uint(nz)) ? 1.f : 0.f;
 }
 
 // Depth of the per-thread staging ring: a chunk's source ranges are fetched

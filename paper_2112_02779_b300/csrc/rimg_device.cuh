@@ -121,6 +121,9 @@ __device__ __forceinline__ bool project_px(const DevLevel& L, float3 x, int proj
   return project_px<R0>(L, x, proj_iters, u, v, r);
 }
 
-__device__ __forceinline__ bool range_ok(float r) { return r > 0.f && r < INFINITY; }
+// 0 < r < inf, as one unsigned comparison on the bit pattern: the positive
+// finite floats are exactly the patterns 1 .. 0x7f7fffff (NaN, +-inf, +-0 and
+// negative values fall outside; checked over all 2^32 patterns).
+__device__ __forceinline__ bool range_ok(float r) { return __float_as_uint(r) - 1u < 0x7f7fffffu; }
 
 }  // namespace rimg
