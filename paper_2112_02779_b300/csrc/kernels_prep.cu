@@ -295,7 +295,7 @@ struct Row4 {
   float4 p[4];   // x, y, z, range of the lane's four pixels
 };
 
-__global__ void __launch_bounds__(32 * NC_WARPS) k_normals_cross(DevLevel L, int levels, int n_img,
+__global__ void __launch_bounds__(32 * NC_WARPS, 4) k_normals_cross(DevLevel L, int levels, int n_img,
                                                                  const float* __restrict__ range, float rel_jump,
                                                                  PlaneOut out, uint8_t* __restrict__ mask0) {
   const int H = L.H, W = L.W;
