@@ -472,6 +472,18 @@ def run_ours(args):
     del ws
     if rank != 0:
         return 0
+    # The kernel is issue-bound (ncu: DRAM ~25 %, issue ~61-65 % of peak): the same launch
+    # against the instruction-issue rate, with the instructions per pixel of the committed
+    # ncu summary (None once the kernel sources no longer hash to the captured version).
+    ipp = profile_value("icp_step_level0_64x1024.md", "instructions_per_pixel",
+                        ("kernel_icp.cu", "rimg_device.cuh", "rimg_internal.h"))
+    issue_peak_t = 148 * 4 * 32 * 2.032 / 1e3      # T thread-instructions/s: SMs x schedulers x lanes x max clock
+    px_per_s = alone_bytes / 20.0 / (ms_l0_alone / 1e3)
+    issue_view = {"bound": "alu", "achieved": (px_per_s * ipp / 1e12) if ipp else None, "peak": issue_peak_t,
+                  "unit": "T thread-instructions/s", "frac": (px_per_s * ipp / 1e12 / issue_peak_t) if ipp else None,
+                  "instructions_per_pixel": ipp,
+                  "how": "pixels/s of the standalone launch x thread instructions per pixel (ncu summary) against "
+                         "148 SMs x 4 schedulers x 32 lanes x 2.032 GHz"}
     line = {
         "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
         "warmup": warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -486,7 +498,8 @@ def run_ours(args):
                                  "busy_ms": l0_union,
                                  "how": "level-0 k_icp bytes of the timed steps over the union of their launch "
                                         "intervals (CUDA events around each launch, timed region 2); the other "
-                                        "sub-batch streams' kernels run concurrently"}},
+                                        "sub-batch streams' kernels run concurrently"},
+                     "issue": issue_view},
         "kernels": kernels,
         "profiled_ms_per_step": ms_profiled / args.steps,
         "e2e": e2e,
