@@ -496,11 +496,13 @@ def icp_step(src_pts, src_valid, target, level, T, params):
 
 
 def register(src_range, dst_range, src_sensor, dst_sensor, T_init, levels, iters, params,
-             return_history=False):
+             return_history=False, return_poses=False):
     """Multi-scale registration: for each level from coarsest to finest run
     the scheduled number of Gauss-Newton steps; the pose carries over between
     levels unchanged.  ``iters`` is listed coarse -> fine.  Sensors are
-    (phi_lut, theta_lut, r0) tuples."""
+    (phi_lut, theta_lut, r0) tuples.  return_history adds every step's
+    record (poses and terms); return_poses adds only the list of the poses
+    after each step (the initial pose first)."""
     assert len(iters) == levels
     sp, st, sr0 = src_sensor
     target = Target(dst_range, *dst_sensor, levels, params.get("normal_rel_jump", np.float32(0.1)),
@@ -508,6 +510,7 @@ def register(src_range, dst_range, src_sensor, dst_sensor, T_init, levels, iters
     T = np.array(T_init, np.float64)
     degenerate = False
     hist = []
+    poses = [T]
     for k, l in enumerate(range(levels - 1, -1, -1)):
         P, sv = source_points(src_range, sp, st, sr0, l)
         for _ in range(iters[k]):
@@ -516,8 +519,12 @@ def register(src_range, dst_range, src_sensor, dst_sensor, T_init, levels, iters
             degenerate |= not ok
             if return_history:
                 hist.append(dict(level=l, T_in=T_prev, T_out=T, terms=terms, ok=ok))
+            if return_poses:
+                poses.append(T)
     if return_history:
         return T, degenerate, hist
+    if return_poses:
+        return T, degenerate, poses
     return T, degenerate
 
 
