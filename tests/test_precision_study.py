@@ -59,8 +59,19 @@ def test_precision_kahan_vs_plain_fp32():
     src, dst, Tgt = make_pairs(cfg, range(n), processes=procs)
     t0 = time.time()
     import multiprocessing as mp
-    with mp.get_context("spawn").Pool(procs) as pool:
-        out = pool.map(_oracle_one, [(src[i], dst[i], CFG) for i in range(n)])
+    # one BLAS / OpenMP thread per spawned worker (they import numpy with this environment)
+    env = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in env}
+    os.environ.update({k: "1" for k in env})
+    try:
+        with mp.get_context("spawn").Pool(procs) as pool:
+            out = pool.map(_oracle_one, [(src[i], dst[i], CFG) for i in range(n)])
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
     To = [o[0] for o in out]
     last = np.array([o[1] for o in out])
     tail = np.array([o[2] for o in out])
