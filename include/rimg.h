@@ -47,7 +47,7 @@ typedef enum rimg_status {
 } rimg_status;
 
 /* Per-pair status bits written by rimg_icp_step / rimg_register. */
-#define RIMG_FLAG_DEGENERATE 1    /* an iteration had < 6 correspondences or a Cholesky pivot
+#define RIMG_FLAG_DEGENERATE 1    /* an iteration had < 6 correspondences or an LDL^T pivot
                                      <= 1e-12 * trace(J^T W J); its update was skipped */
 
 /* One pyramid level of a sensor's device tables (filled by rimg_sensor_build;
@@ -200,7 +200,7 @@ int rimg_normals(const rimg_sensor* s, int n_images, const float* range, const r
  *   J^T W J (21 upper-triangle terms, row-major), J^T W e (6), sum w e^2, count
  * (29 values, FP32 per thread with optional Kahan compensation, FP64 across
  * blocks).  With `update` != 0 it solves (J^T W J) xi = -J^T W e by an FP64
- * Cholesky factorisation and sets T <- Exp(xi) T in place; a degenerate system
+ * LDL^T (Cholesky-type) factorisation and sets T <- Exp(xi) T in place; a degenerate system
  * (count < 6 or pivot <= 1e-12 trace) leaves T unchanged and sets
  * RIMG_FLAG_DEGENERATE in status[pair] (status is OR-ed, never cleared here).
  *
