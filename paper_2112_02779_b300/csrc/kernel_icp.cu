@@ -202,22 +202,26 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
 // The 29 reduced quantities live in 15 float2 accumulators (30 lanes):
-// lane index f = 2 * pair + (0 for .x, 1 for .y).  kFlat maps the output
-// order (21 upper-triangle J^T W J entries row-major, 6 J^T W e, sum w e^2,
-// count) to lanes.
+// lane index f = 2 * pair + (0 for .x, 1 for .y).  Pairs 0..8 are updated by
+// packed FP32x2 FMAs whose operands are register pairs that arise without
+// moves -- (a0, a1) and (a2, e) as computed, (nx, ny) as loaded -- plus the
+// swaps (ny, nx) and (e, a2); pairs 9..13 hold scalar FMAs, pair 14 the count.
+// kFlat maps the output order (21 upper-triangle J^T W J entries row-major,
+// 6 J^T W e, sum w e^2, count) to lanes.
 constexpr int kPairs = 15;
-__constant__ int kFlat[kRed] = {0,  18, 2,  12, 4,  14,  // H00..H05
-                                1,  13, 3,  15, 5,       // H11..H15
-                                6,  19, 8,  16,          // H22..H25
-                                7,  17, 9,               // H33..H35
-                                10, 20,                  // H44, H45
-                                11,                      // H55
-                                22, 23, 24, 25, 26, 27,  // g0..g5
-                                21, 28};                 // sum w e^2, count
+__constant__ int kFlat[kRed] = {0,  18, 2,  4,  6,  19,  // H00..H05
+                                1,  9,  7,  5,  20,      // H11..H15
+                                10, 12, 14, 21,          // H22..H25
+                                16, 22, 23,              // H33..H35
+                                17, 24,                  // H44, H45
+                                25,                      // H55
+                                8,  3,  26, 15, 13, 27,  // g0..g5
+                                11, 28};                 // sum w e^2, count
 
 // Point-to-plane terms of one association: residual e = n.x - d, IRLS weight,
-// J = [x cross n, n]; adds w J J^T (upper triangle), w e J, w e^2 and the
-// count into t.  A zero plane (no association) contributes exactly nothing.
+// J = [a, n] with a = x cross n; adds w J J^T (upper triangle), w e J, w e^2
+// and the count into t.  A zero plane (no association) contributes exactly
+// nothing.
 __device__ __forceinline__ void accumulate_px(float2 (&t)[kPairs], float x, float y, float z, float4 pl,
                                               float inv_delta) {
   const float nx = pl.x, ny = pl.y, nz = pl.z;
@@ -227,25 +231,31 @@ __device__ __forceinline__ void accumulate_px(float2 (&t)[kPairs], float x, floa
     const float q = e * inv_delta;
     w = rsqrtf(fmaf(q, q, 1.f));
   }
-  const float J0 = fmaf(y, nz, -z * ny), J1 = fmaf(z, nx, -x * nz), J2 = fmaf(x, ny, -y * nx);
-  const float2 J01 = f2(J0, J1), J23 = f2(J2, nx), J45 = f2(ny, nz);
+  const float a0 = fmaf(y, nz, -z * ny), a1 = fmaf(z, nx, -x * nz), a2 = fmaf(x, ny, -y * nx);
+  const float2 P1 = f2(a0, a1), P2 = f2(a2, e), N1 = f2(nx, ny);
+  const float2 M1 = f2(ny, nx), S2 = f2(e, a2);
   const float2 W2 = f2(w, w);
-  const float2 U01 = mul2(W2, J01), U23 = mul2(W2, J23), U45 = mul2(W2, J45);
-  const float2 E2 = f2(e, e);
-  t[0] = fma2(U01, J01, t[0]);                         // H00 H11
-  t[1] = fma2(U01, J23, t[1]);                         // H02 H13
-  t[2] = fma2(U01, J45, t[2]);                         // H04 H15
-  t[3] = fma2(U23, J23, t[3]);                         // H22 H33
-  t[4] = fma2(U23, J45, t[4]);                         // H24 H35
-  t[5] = fma2(U45, J45, t[5]);                         // H44 H55
-  t[6] = fma2(U01, f2(nx, J2), t[6]);                  // H03 H12
-  t[7] = fma2(U01, f2(nz, ny), t[7]);                  // H05 H14
-  t[8] = fma2(U23, f2(nz, ny), t[8]);                  // H25 H34
-  t[9] = fma2(f2(U01.x, U23.x), f2(J1, nx), t[9]);     // H01 H23
-  t[10] = fma2(f2(U45.x, w * e), f2(nz, e), t[10]);    // H45, w e^2
-  t[11] = fma2(U01, E2, t[11]);                        // g0 g1
-  t[12] = fma2(U23, E2, t[12]);                        // g2 g3
-  t[13] = fma2(U45, E2, t[13]);                        // g4 g5
+  const float2 UP1 = mul2(W2, P1), UP2 = mul2(W2, P2), UN1 = mul2(W2, N1);
+  const float wnz = w * nz;
+  t[0] = fma2(UP1, P1, t[0]);                          // H00 H11
+  t[1] = fma2(UP1, P2, t[1]);                          // H02 g1
+  t[2] = fma2(UP1, N1, t[2]);                          // H03 H14
+  t[3] = fma2(UP1, M1, t[3]);                          // H04 H13
+  t[4] = fma2(UP1, S2, t[4]);                          // g0 H12
+  t[5] = fma2(UP2, P2, t[5]);                          // H22, w e^2
+  t[6] = fma2(UP2, N1, t[6]);                          // H23 g4
+  t[7] = fma2(UP2, M1, t[7]);                          // H24 g3
+  t[8] = fma2(UN1, N1, t[8]);                          // H33 H44
+  t[9].x = fmaf(UP1.x, a1, t[9].x);                    // H01
+  t[9].y = fmaf(UP1.x, nz, t[9].y);                    // H05
+  t[10].x = fmaf(UP1.y, nz, t[10].x);                  // H15
+  t[10].y = fmaf(UP2.x, nz, t[10].y);                  // H25
+  t[11].x = fmaf(UN1.x, ny, t[11].x);                  // H34
+  t[11].y = fmaf(UN1.x, nz, t[11].y);                  // H35
+  t[12].x = fmaf(UN1.y, nz, t[12].x);                  // H45
+  t[12].y = fmaf(wnz, nz, t[12].y);                    // H55
+  t[13].x = fmaf(UP2.x, e, t[13].x);                   // g2
+  t[13].y = fmaf(wnz, e, t[13].y);                     // g5
   // an association counts when its plane is not the all-zero invalid plane
   // (stored as +0.f; a unit normal has a non-zero component)
   t[14].x += (__float_as_uint(nx) | __float_as_uint(ny) | __float_as_uint(nz)) ? 1.f : 0.f;
