@@ -323,7 +323,9 @@ __device__ __forceinline__ float warp_scatter_sum(const float2 (&t)[kPairs], int
 // One block's share of a step: the rows [v_begin, v_end) of pair `pair` at
 // the pose in sm.T4.  On return (after a block barrier) sm.red[w][l] holds
 // warp w's component l of the 29 sums (lane order, see kFlat).
-template <bool R0, bool GATE, bool ASSOC, bool KAHAN, int THREADS>
+// ROWSTRIDE: the thread stride is a whole number of rows (chunks per row
+// divide THREADS), so a cursor advances by rows only.
+template <bool R0, bool GATE, bool ASSOC, bool KAHAN, int THREADS, bool ROWSTRIDE = false>
 __device__ __forceinline__ void icp_block_terms(const IcpLaunch& a, IcpSmem<THREADS>& sm, int pair, int v_begin,
                                                 int v_end) {
   const int tid = threadIdx.x;
@@ -359,9 +361,13 @@ __device__ __forceinline__ void icp_block_terms(const IcpLaunch& a, IcpSmem<THRE
   };
   const Cursor start{v_begin + tid / cpr, tid - (tid / cpr) * cpr};
   auto advance = [&](Cursor& k) {
-    k.cu += dcu;
-    k.v += dv;
-    if (k.cu >= cpr) { k.cu -= cpr; ++k.v; }
+    if (ROWSTRIDE) {
+      k.v += dv;
+    } else {
+      k.cu += dcu;
+      k.v += dv;
+      if (k.cu >= cpr) { k.cu -= cpr; ++k.v; }
+    }
   };
   Cursor cf = start, ci = start, cc = start;   // fetch, issue, consume
 
@@ -523,7 +529,7 @@ __device__ __forceinline__ float block_total(const IcpSmem<THREADS>& sm, int tid
   return acc;
 }
 
-template <bool R0, bool GATE, bool ASSOC, bool KAHAN, int THREADS>
+template <bool R0, bool GATE, bool ASSOC, bool KAHAN, int THREADS, bool ROWSTRIDE = false>
 __global__ void __launch_bounds__(THREADS, RIMG_ICP_THREADS_PER_SM / THREADS) k_icp(IcpLaunch a) {
   extern __shared__ float4 smem_raw[];
   IcpSmem<THREADS>& sm = *reinterpret_cast<IcpSmem<THREADS>*>(smem_raw);
@@ -533,7 +539,8 @@ __global__ void __launch_bounds__(THREADS, RIMG_ICP_THREADS_PER_SM / THREADS) k_
   if (tid < 12) reinterpret_cast<float*>(sm.T4)[tid] = (float)a.pose[pair * 16 + tid];
   __syncthreads();
   const int v_begin = blk * a.rows_per_block;
-  icp_block_terms<R0, GATE, ASSOC, KAHAN, THREADS>(a, sm, pair, v_begin, min(a.src.H, v_begin + a.rows_per_block));
+  icp_block_terms<R0, GATE, ASSOC, KAHAN, THREADS, ROWSTRIDE>(a, sm, pair, v_begin,
+                                                              min(a.src.H, v_begin + a.rows_per_block));
   if (a.bpp == 1) {
     // one block per pair: the block total is the pair total
     if (tid < kRed) {
@@ -610,7 +617,7 @@ __global__ void __launch_bounds__(128) k_solve(int n_pairs, double* sums, double
 // level whose pair fits one block collapse into one.  Same arithmetic as
 // k_icp with one block per pair followed by k_solve.  The pair's final sums
 // and step record are left in a.sums (as after the last k_solve).
-template <bool R0, bool GATE, bool KAHAN, int THREADS>
+template <bool R0, bool GATE, bool KAHAN, int THREADS, bool ROWSTRIDE = false>
 __global__ void __launch_bounds__(THREADS, RIMG_ICP_THREADS_PER_SM / THREADS) k_icp_iters(IcpLaunch a, int iters) {
   extern __shared__ float4 smem_raw[];
   IcpSmem<THREADS>& sm = *reinterpret_cast<IcpSmem<THREADS>*>(smem_raw);
@@ -625,7 +632,7 @@ __global__ void __launch_bounds__(THREADS, RIMG_ICP_THREADS_PER_SM / THREADS) k_
   if (tid == 0) degenerate = 0;
   __syncthreads();
   for (int it = 0; it < iters; ++it) {
-    icp_block_terms<R0, GATE, false, KAHAN, THREADS>(a, sm, pair, 0, a.src.H);
+    icp_block_terms<R0, GATE, false, KAHAN, THREADS, ROWSTRIDE>(a, sm, pair, 0, a.src.H);
     if (tid < kRed) sm.tot[tid] = (double)block_total(sm, tid);
     __syncthreads();
     if (tid < 32) {
@@ -722,18 +729,33 @@ void icp_grid(int H, int W, int n_pairs, int* bpp, int* rows_per_block, int* thr
   *threads = T;
 }
 
-template <bool R0, bool GATE, bool ASSOC, bool KAHAN, int T>
-cudaError_t launch_icp_t(const IcpLaunch& a, long long blocks, cudaStream_t st) {
+// Whether a thread stride of T chunks is a whole number of rows of the level.
+inline bool row_stride(const IcpLaunch& a, int T) {
+  const int cpr = a.src.W >> 2;
+  return cpr > 0 && cpr <= T && T % cpr == 0;
+}
+
+template <bool R0, bool GATE, bool ASSOC, bool KAHAN, int T, bool ROWSTRIDE>
+cudaError_t launch_icp_ts(const IcpLaunch& a, long long blocks, cudaStream_t st) {
   constexpr size_t bytes = sizeof(IcpSmem<T>);
   static bool configured = false;   // per instantiation; the attribute is per function
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_icp<R0, GATE, ASSOC, KAHAN, T>,
+    cudaError_t e = cudaFuncSetAttribute(k_icp<R0, GATE, ASSOC, KAHAN, T, ROWSTRIDE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  k_icp<R0, GATE, ASSOC, KAHAN, T><<<(unsigned)blocks, T, bytes, st>>>(a);
+  k_icp<R0, GATE, ASSOC, KAHAN, T, ROWSTRIDE><<<(unsigned)blocks, T, bytes, st>>>(a);
   return cudaGetLastError();
+}
+
+// the row-stride form only on the default path (no gate, no association output)
+template <bool R0, bool GATE, bool ASSOC, bool KAHAN, int T>
+cudaError_t launch_icp_t(const IcpLaunch& a, long long blocks, cudaStream_t st) {
+  if constexpr (!GATE && !ASSOC) {
+    if (row_stride(a, T)) return launch_icp_ts<R0, GATE, ASSOC, KAHAN, T, true>(a, blocks, st);
+  }
+  return launch_icp_ts<R0, GATE, ASSOC, KAHAN, T, false>(a, blocks, st);
 }
 
 template <bool R0, bool GATE, bool ASSOC, bool KAHAN>
@@ -742,18 +764,26 @@ cudaError_t launch_icp_k(const IcpLaunch& a, long long blocks, cudaStream_t st) 
                           : launch_icp_t<R0, GATE, ASSOC, KAHAN, 256>(a, blocks, st);
 }
 
-template <bool R0, bool GATE, bool KAHAN, int T>
-cudaError_t launch_icp_iters_t(const IcpLaunch& a, int iters, cudaStream_t st) {
+template <bool R0, bool GATE, bool KAHAN, int T, bool ROWSTRIDE>
+cudaError_t launch_icp_iters_ts(const IcpLaunch& a, int iters, cudaStream_t st) {
   constexpr size_t bytes = sizeof(IcpSmem<T>);
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_icp_iters<R0, GATE, KAHAN, T>,
+    cudaError_t e = cudaFuncSetAttribute(k_icp_iters<R0, GATE, KAHAN, T, ROWSTRIDE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  k_icp_iters<R0, GATE, KAHAN, T><<<(unsigned)a.n_pairs, T, bytes, st>>>(a, iters);
+  k_icp_iters<R0, GATE, KAHAN, T, ROWSTRIDE><<<(unsigned)a.n_pairs, T, bytes, st>>>(a, iters);
   return cudaGetLastError();
+}
+
+template <bool R0, bool GATE, bool KAHAN, int T>
+cudaError_t launch_icp_iters_t(const IcpLaunch& a, int iters, cudaStream_t st) {
+  if constexpr (!GATE) {
+    if (row_stride(a, T)) return launch_icp_iters_ts<R0, GATE, KAHAN, T, true>(a, iters, st);
+  }
+  return launch_icp_iters_ts<R0, GATE, KAHAN, T, false>(a, iters, st);
 }
 
 template <bool R0, bool GATE, bool KAHAN>
