@@ -285,9 +285,10 @@ struct IcpSmem {
 
 // Chunks summed plainly per thread between two compensated warp steps.
 #ifndef RIMG_WARP_FLUSH
-#define RIMG_WARP_FLUSH 4
+#define RIMG_WARP_FLUSH 8
 #endif
 constexpr int kWarpFlush = RIMG_WARP_FLUSH;
+static_assert(kWarpFlush >= 1, "at least one chunk between warp steps");
 
 // Reduce-scatter of the 30 lanes of t (15 float2, padded to 16) across the
 // warp: lane l receives the warp's sum of component l (component f is lane
@@ -510,7 +511,9 @@ __device__ __forceinline__ void icp_block_terms(const IcpLaunch& a, IcpSmem<THRE
     if (i >= nwarp) break;
     ++i;
   }
-  warp_flush();
+  // the last step flushed already when nwarp is a multiple of kWarpFlush
+  // (nwarp = 0: nothing was summed)
+  if ((nwarp % kWarpFlush) != 0) warp_flush();
   asm volatile("cp.async.wait_all;\n" ::: "memory");
 
   // lane l holds the warp's component l
