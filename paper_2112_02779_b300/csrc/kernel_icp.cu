@@ -226,11 +226,9 @@ __device__ __forceinline__ void accumulate_px(float2 (&t)[kPairs], float x, floa
                                               float inv_delta) {
   const float nx = pl.x, ny = pl.y, nz = pl.z;
   const float e = fmaf(nx, x, fmaf(ny, y, fmaf(nz, z, -pl.w)));
-  float w = 1.f;
-  if (inv_delta > 0.f) {
-    const float q = e * inv_delta;
-    w = rsqrtf(fmaf(q, q, 1.f));
-  }
+  // a select, not a branch, so that the four pixels of a chunk stay one block
+  const float q = e * inv_delta;
+  const float w = inv_delta > 0.f ? rsqrtf(fmaf(q, q, 1.f)) : 1.f;
   const float a0 = fmaf(y, nz, -z * ny), a1 = fmaf(z, nx, -x * nz), a2 = fmaf(x, ny, -y * nx);
   const float2 P1 = f2(a0, a1), P2 = f2(a2, e), N1 = f2(nx, ny);
   const float2 M1 = f2(ny, nx), S2 = f2(e, a2);
@@ -325,8 +323,10 @@ __device__ __forceinline__ float warp_scatter_sum(const float2 (&t)[kPairs], int
 // the pose in sm.T4.  On return (after a block barrier) sm.red[w][l] holds
 // warp w's component l of the 29 sums (lane order, see kFlat).
 // ROWSTRIDE: the thread stride is a whole number of rows (chunks per row
-// divide THREADS), so a cursor advances by rows only.
-template <bool R0, bool GATE, bool ASSOC, bool KAHAN, int THREADS, bool ROWSTRIDE = false>
+// divide THREADS), so a cursor advances by rows only.  FAST: the target
+// level's inverse table is exact and it has no azimuth offsets (the
+// projection has no branch).
+template <bool R0, bool GATE, bool ASSOC, bool KAHAN, int THREADS, bool ROWSTRIDE = false, bool FAST = false>
 __device__ __forceinline__ void icp_block_terms(const IcpLaunch& a, IcpSmem<THREADS>& sm, int pair, int v_begin,
                                                 int v_end) {
   const int tid = threadIdx.x;
@@ -418,7 +418,7 @@ __device__ __forceinline__ void icp_block_terms(const IcpLaunch& a, IcpSmem<THRE
       const float Y = fmaf(r, Dy, oy);
       const float Z = fmaf(r, Dz, oz);
       int uu, vv;
-      const bool fov = project_px<R0>(D, make_float3(X, Y, Z), a.proj_iters, uu, vv);
+      const bool fov = project_px<R0, FAST>(D, make_float3(X, Y, Z), a.proj_iters, uu, vv);
       const bool ok = valid && fov;
       const int idx = vv * D.W + uu;
       cp_async16_zfill(&sm.planes[slot][q][tid], planes + idx, ok);
@@ -532,7 +532,7 @@ __device__ __forceinline__ float block_total(const IcpSmem<THREADS>& sm, int tid
   return acc;
 }
 
-template <bool R0, bool GATE, bool ASSOC, bool KAHAN, int THREADS, bool ROWSTRIDE = false>
+template <bool R0, bool GATE, bool ASSOC, bool KAHAN, int THREADS, bool ROWSTRIDE = false, bool FAST = false>
 __global__ void __launch_bounds__(THREADS, RIMG_ICP_THREADS_PER_SM / THREADS) k_icp(IcpLaunch a) {
   extern __shared__ float4 smem_raw[];
   IcpSmem<THREADS>& sm = *reinterpret_cast<IcpSmem<THREADS>*>(smem_raw);
@@ -542,8 +542,8 @@ __global__ void __launch_bounds__(THREADS, RIMG_ICP_THREADS_PER_SM / THREADS) k_
   if (tid < 12) reinterpret_cast<float*>(sm.T4)[tid] = (float)a.pose[pair * 16 + tid];
   __syncthreads();
   const int v_begin = blk * a.rows_per_block;
-  icp_block_terms<R0, GATE, ASSOC, KAHAN, THREADS, ROWSTRIDE>(a, sm, pair, v_begin,
-                                                              min(a.src.H, v_begin + a.rows_per_block));
+  icp_block_terms<R0, GATE, ASSOC, KAHAN, THREADS, ROWSTRIDE, FAST>(a, sm, pair, v_begin,
+                                                                    min(a.src.H, v_begin + a.rows_per_block));
   if (a.bpp == 1) {
     // one block per pair: the block total is the pair total
     if (tid < kRed) {
@@ -620,7 +620,7 @@ __global__ void __launch_bounds__(128) k_solve(int n_pairs, double* sums, double
 // level whose pair fits one block collapse into one.  Same arithmetic as
 // k_icp with one block per pair followed by k_solve.  The pair's final sums
 // and step record are left in a.sums (as after the last k_solve).
-template <bool R0, bool GATE, bool KAHAN, int THREADS, bool ROWSTRIDE = false>
+template <bool R0, bool GATE, bool KAHAN, int THREADS, bool ROWSTRIDE = false, bool FAST = false>
 __global__ void __launch_bounds__(THREADS, RIMG_ICP_THREADS_PER_SM / THREADS) k_icp_iters(IcpLaunch a, int iters) {
   extern __shared__ float4 smem_raw[];
   IcpSmem<THREADS>& sm = *reinterpret_cast<IcpSmem<THREADS>*>(smem_raw);
@@ -635,7 +635,7 @@ __global__ void __launch_bounds__(THREADS, RIMG_ICP_THREADS_PER_SM / THREADS) k_
   if (tid == 0) degenerate = 0;
   __syncthreads();
   for (int it = 0; it < iters; ++it) {
-    icp_block_terms<R0, GATE, false, KAHAN, THREADS, ROWSTRIDE>(a, sm, pair, 0, a.src.H);
+    icp_block_terms<R0, GATE, false, KAHAN, THREADS, ROWSTRIDE, FAST>(a, sm, pair, 0, a.src.H);
     if (tid < kRed) sm.tot[tid] = (double)block_total(sm, tid);
     __syncthreads();
     if (tid < 32) {
@@ -738,25 +738,33 @@ inline bool row_stride(const IcpLaunch& a, int T) {
   return cpr > 0 && cpr <= T && T % cpr == 0;
 }
 
-template <bool R0, bool GATE, bool ASSOC, bool KAHAN, int T, bool ROWSTRIDE>
+// Whether the target level's projection needs neither the boundary walk nor
+// the azimuth offsets.
+inline bool fast_projection(const IcpLaunch& a) { return a.dst.bins_exact && !a.dst.has_theta; }
+
+template <bool R0, bool GATE, bool ASSOC, bool KAHAN, int T, bool ROWSTRIDE, bool FAST = false>
 cudaError_t launch_icp_ts(const IcpLaunch& a, long long blocks, cudaStream_t st) {
   constexpr size_t bytes = sizeof(IcpSmem<T>);
   static bool configured = false;   // per instantiation; the attribute is per function
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_icp<R0, GATE, ASSOC, KAHAN, T, ROWSTRIDE>,
+    cudaError_t e = cudaFuncSetAttribute(k_icp<R0, GATE, ASSOC, KAHAN, T, ROWSTRIDE, FAST>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  k_icp<R0, GATE, ASSOC, KAHAN, T, ROWSTRIDE><<<(unsigned)blocks, T, bytes, st>>>(a);
+  k_icp<R0, GATE, ASSOC, KAHAN, T, ROWSTRIDE, FAST><<<(unsigned)blocks, T, bytes, st>>>(a);
   return cudaGetLastError();
 }
 
-// the row-stride form only on the default path (no gate, no association output)
+// the row-stride and fast-projection forms only on the default path (no gate,
+// no association output)
 template <bool R0, bool GATE, bool ASSOC, bool KAHAN, int T>
 cudaError_t launch_icp_t(const IcpLaunch& a, long long blocks, cudaStream_t st) {
   if constexpr (!GATE && !ASSOC) {
-    if (row_stride(a, T)) return launch_icp_ts<R0, GATE, ASSOC, KAHAN, T, true>(a, blocks, st);
+    if (row_stride(a, T)) {
+      if (fast_projection(a)) return launch_icp_ts<R0, GATE, ASSOC, KAHAN, T, true, true>(a, blocks, st);
+      return launch_icp_ts<R0, GATE, ASSOC, KAHAN, T, true>(a, blocks, st);
+    }
   }
   return launch_icp_ts<R0, GATE, ASSOC, KAHAN, T, false>(a, blocks, st);
 }
@@ -767,24 +775,27 @@ cudaError_t launch_icp_k(const IcpLaunch& a, long long blocks, cudaStream_t st) 
                           : launch_icp_t<R0, GATE, ASSOC, KAHAN, 256>(a, blocks, st);
 }
 
-template <bool R0, bool GATE, bool KAHAN, int T, bool ROWSTRIDE>
+template <bool R0, bool GATE, bool KAHAN, int T, bool ROWSTRIDE, bool FAST = false>
 cudaError_t launch_icp_iters_ts(const IcpLaunch& a, int iters, cudaStream_t st) {
   constexpr size_t bytes = sizeof(IcpSmem<T>);
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_icp_iters<R0, GATE, KAHAN, T, ROWSTRIDE>,
+    cudaError_t e = cudaFuncSetAttribute(k_icp_iters<R0, GATE, KAHAN, T, ROWSTRIDE, FAST>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  k_icp_iters<R0, GATE, KAHAN, T, ROWSTRIDE><<<(unsigned)a.n_pairs, T, bytes, st>>>(a, iters);
+  k_icp_iters<R0, GATE, KAHAN, T, ROWSTRIDE, FAST><<<(unsigned)a.n_pairs, T, bytes, st>>>(a, iters);
   return cudaGetLastError();
 }
 
 template <bool R0, bool GATE, bool KAHAN, int T>
 cudaError_t launch_icp_iters_t(const IcpLaunch& a, int iters, cudaStream_t st) {
   if constexpr (!GATE) {
-    if (row_stride(a, T)) return launch_icp_iters_ts<R0, GATE, KAHAN, T, true>(a, iters, st);
+    if (row_stride(a, T)) {
+      if (fast_projection(a)) return launch_icp_iters_ts<R0, GATE, KAHAN, T, true, true>(a, iters, st);
+      return launch_icp_iters_ts<R0, GATE, KAHAN, T, true>(a, iters, st);
+    }
   }
   return launch_icp_iters_ts<R0, GATE, KAHAN, T, false>(a, iters, st);
 }

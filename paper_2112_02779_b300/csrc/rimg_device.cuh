@@ -24,11 +24,13 @@ __device__ __forceinline__ float3 unproject_px(const DevLevel& L, int u, int v, 
 // picks the row below or above; the tie rule (exact ties go to the lower row
 // index) is folded into the stored boundary.  For tables too uneven for that,
 // the walk across the sorted boundaries (bounded by H) gives the same argmin.
+// EXACT: the caller knows the table is exact (no walk, no branch).
+template <bool EXACT = false>
 __device__ __forceinline__ int row_from_sin(const DevLevel& L, float s) {
   int b = __float2int_rd((s - L.s_lo) * L.bin_scale);
   b = min(max(b, 0), L.n_bins - 1);
   const int4 e = __ldg(L.bins + b);
-  if (L.bins_exact) return (s > __int_as_float(e.z)) ? e.y : e.x;   // tie rule folded into the boundary
+  if (EXACT || L.bins_exact) return (s > __int_as_float(e.z)) ? e.y : e.x;   // tie rule folded into the boundary
   int j = e.w;
   if (L.tie_up) {
     for (int k = 0; k < L.H && j < L.H - 1 && s >= __ldg(L.bnd + j); ++k) ++j;
@@ -77,8 +79,10 @@ __device__ __forceinline__ int wrap_col(float uc, int W) {
 // Pi (Section 3.2) of point x into level L.  Returns true when the point lies
 // inside the vertical field of view; (u, v) are always valid indices and r is
 // the point's range from the receiver (|x - o| with the receiver offset o of
-// the last fixed-point step).
-template <bool R0>
+// the last fixed-point step).  FAST: the caller knows that L's inverse table
+// is exact and that L has no azimuth offsets (theta_lut = 0), so the
+// projection is one straight-line block.
+template <bool R0, bool FAST = false>
 __device__ __forceinline__ bool project_px(const DevLevel& L, float3 x, int proj_iters, int& u, int& v,
                                            float& r) {
   float s;
@@ -87,9 +91,9 @@ __device__ __forceinline__ bool project_px(const DevLevel& L, float3 x, int proj
     const float inv = rsqrtf(n2);
     s = x.z * inv;
     r = n2 * inv;
-    v = row_from_sin(L, s);
+    v = row_from_sin<FAST>(L, s);
     float uc = atan2_poly(x.y, x.x) * L.w_over_2pi;
-    if (L.has_theta) uc -= __ldg(L.thu + v);
+    if (!FAST && L.has_theta) uc -= __ldg(L.thu + v);
     u = wrap_col(uc, L.W);
   } else {
     // receiver-offset fixed point on the column angle 2 pi u_c / W
@@ -106,19 +110,19 @@ __device__ __forceinline__ bool project_px(const DevLevel& L, float3 x, int proj
       const float inv = rsqrtf(n2);
       s = x.z * inv;
       r = n2 * inv;
-      v = row_from_sin(L, s);
+      v = row_from_sin<FAST>(L, s);
       uc = atan2_poly(yp, xp) * L.w_over_2pi;
-      if (L.has_theta) uc -= __ldg(L.thu + v);
+      if (!FAST && L.has_theta) uc -= __ldg(L.thu + v);
     }
     u = wrap_col(uc, L.W);
   }
   return (s >= L.s_lo) && (s <= L.s_hi);   // false for NaN
 }
 
-template <bool R0>
+template <bool R0, bool FAST = false>
 __device__ __forceinline__ bool project_px(const DevLevel& L, float3 x, int proj_iters, int& u, int& v) {
   float r;
-  return project_px<R0>(L, x, proj_iters, u, v, r);
+  return project_px<R0, FAST>(L, x, proj_iters, u, v, r);
 }
 
 // 0 < r < inf, as one unsigned comparison on the bit pattern: the positive

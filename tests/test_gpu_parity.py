@@ -153,7 +153,7 @@ def test_normals_parity_strip_edges(R, H, W, levels):
 
 # ---------------------------------------------------------------------------
 def _icp_case(R, name, levels, level, pose_kind, params_kw=None, idx=0):
-    cfg = CONFIGS[name]
+    cfg = CONFIGS[name] if isinstance(name, str) else name
     pair = make_pair(cfg, idx)
     s = pair["sensor"]
     sens = gpu_sensor(R, s, levels)
@@ -198,11 +198,9 @@ def _sum_bounds(terms, n_mismatch, rel=1e-3):
     return np.concatenate([rel * s + 2 * n_mismatch * m, [n_mismatch]])
 
 
-@pytest.mark.parametrize("name,levels", CFG_LEVELS)
-@pytest.mark.parametrize("pose_kind", ["identity", "near"])
-def test_icp_step_parity(R, name, levels, pose_kind):
+def _check_icp_levels(R, cfg, levels, pose_kind):
     for level in range(levels):
-        assoc, out29, terms, T, pose_after = _icp_case(R, name, levels, level, pose_kind)
+        assoc, out29, terms, T, pose_after = _icp_case(R, cfg, levels, level, pose_kind)
         assert np.array_equal(pose_after.reshape(4, 4), T)          # update = 0 leaves the pose alone
         near = terms["near_tie"]
         a_o = terms["assoc"]
@@ -214,6 +212,53 @@ def test_icp_step_parity(R, name, levels, pose_kind):
         bound = _sum_bounds(terms, n_mis)
         err = np.abs(out29 - ref)
         assert np.all(err <= bound + 1e-9), (level, err / np.maximum(bound, 1e-30))
+
+
+@pytest.mark.parametrize("name,levels", CFG_LEVELS)
+@pytest.mark.parametrize("pose_kind", ["identity", "near"])
+def test_icp_step_parity(R, name, levels, pose_kind):
+    _check_icp_levels(R, name, levels, pose_kind)
+
+
+def _fast_projection(sens, level):
+    """Whether the association kernels project into this level without the
+    boundary walk and the azimuth offsets (exact inverse table, theta_lut = 0)."""
+    L = sens.level[level]
+    return bool(L.bins_exact) and not L.has_theta
+
+
+def test_configs_cover_both_projection_forms(R):
+    """The parity configurations reach the branch-free projection (exact
+    tables, no azimuth offsets) and the general one (azimuth offsets, or a
+    table uneven enough to need the boundary walk)."""
+    forms = set()
+    for name, levels in CFG_LEVELS:
+        sens = gpu_sensor(R, CONFIGS[name].sensor(), levels)
+        forms |= {_fast_projection(sens, l) for l in range(levels)}
+    assert forms == {True, False}
+    s = CONFIGS["pair64x1024"].sensor()
+    assert all(_fast_projection(gpu_sensor(R, s, 4), l) for l in range(4))   # the headline sensor
+
+
+@pytest.mark.parametrize("pose_kind", ["identity", "near"])
+def test_icp_step_parity_fast_projection_with_receiver_offset(R, pose_kind):
+    """Exact tables and no azimuth offsets, with a receiver offset r0 = 1.5 cm:
+    the branch-free projection inside the receiver-offset fixed point (every
+    level of one step, then registrations) against the oracle."""
+    import dataclasses
+    cfg = dataclasses.replace(CONFIGS["pair32x512"], name="pair32x512_r0", config_id=91, r0=0.015)
+    sens = gpu_sensor(R, cfg.sensor(), 3)
+    assert all(_fast_projection(sens, l) for l in range(3))
+    _check_icp_levels(R, cfg, 3, pose_kind)
+    if pose_kind == "identity":
+        s = cfg.sensor()
+        params = R.rimg_default_params(huber_delta=cfg.huber_delta)
+        src, dst, _ = make_pairs(cfg, range(3))
+        Tg, _ = gpu_register(R, torch, sens, src, dst, np.tile(np.eye(4), (3, 1, 1)), 3, cfg.iters, params)
+        for i in range(3):
+            To, _ = oracle_register(src[i], dst[i], s, np.eye(4), 3, cfg.iters, oracle_params(cfg))
+            eR, et = O.pose_error(Tg[i], To)
+            assert eR <= 1e-4 and et <= 1e-4, (i, eR, et)
 
 
 def test_icp_step_gate_parity(R):
