@@ -223,7 +223,7 @@ def test_icp_step_parity(R, name, levels, pose_kind):
 def _fast_projection(sens, level):
     """Whether the association kernels project into this level without the
     boundary walk and the azimuth offsets (exact inverse table, theta_lut = 0)."""
-    L = sens.level[level]
+    L = sens.struct.level[level]
     return bool(L.bins_exact) and not L.has_theta
 
 
