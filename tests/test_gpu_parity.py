@@ -253,7 +253,9 @@ def test_icp_step_parity_fast_projection_with_receiver_offset(R, pose_kind):
     if pose_kind == "identity":
         s = cfg.sensor()
         params = R.rimg_default_params(huber_delta=cfg.huber_delta)
-        src, dst, _ = make_pairs(cfg, range(3))
+        pairs = [make_pair(cfg, i) for i in range(3)]   # a derived config: not in the pool's table
+        src = np.stack([q["src_range"] for q in pairs])
+        dst = np.stack([q["dst_range"] for q in pairs])
         Tg, _ = gpu_register(R, torch, sens, src, dst, np.tile(np.eye(4), (3, 1, 1)), 3, cfg.iters, params)
         for i in range(3):
             To, _ = oracle_register(src[i], dst[i], s, np.eye(4), 3, cfg.iters, oracle_params(cfg))
