@@ -324,8 +324,8 @@ __device__ __forceinline__ float warp_scatter_sum(const float2 (&t)[kPairs], int
 // warp w's component l of the 29 sums (lane order, see kFlat).
 // ROWSTRIDE: the thread stride is a whole number of rows (chunks per row
 // divide THREADS), so a cursor advances by rows only.  FAST: the target
-// level's inverse table is exact and it has no azimuth offsets (the
-// projection has no branch).
+// level's inverse table is exact, it has no azimuth offsets and its width is
+// a power of two (the projection has no branch).
 template <bool R0, bool GATE, bool ASSOC, bool KAHAN, int THREADS, bool ROWSTRIDE = false, bool FAST = false>
 __device__ __forceinline__ void icp_block_terms(const IcpLaunch& a, IcpSmem<THREADS>& sm, int pair, int v_begin,
                                                 int v_end) {
@@ -421,12 +421,17 @@ __device__ __forceinline__ void icp_block_terms(const IcpLaunch& a, IcpSmem<THRE
       const bool fov = project_px<R0, FAST>(D, make_float3(X, Y, Z), a.proj_iters, uu, vv);
       const bool ok = valid && fov;
       const int idx = vv * D.W + uu;
-      cp_async16_zfill(&sm.planes[slot][q][tid], planes + idx, ok);
       P.x[q] = X;
       P.y[q] = Y;
       P.z[q] = Z;
       P.idx[q] = ok ? idx : -1;
     }
+    // The gathers after all four projections: each copy is an asm statement
+    // that clobbers memory, so a copy between two projections would keep the
+    // next pixel's table loads from moving above it.
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      cp_async16_zfill(&sm.planes[slot][q][tid], planes + max(P.idx[q], 0), P.idx[q] >= 0);
   };
 
   // The warp's plain sums since the last step, added to each lane's running
@@ -739,8 +744,10 @@ inline bool row_stride(const IcpLaunch& a, int T) {
 }
 
 // Whether the target level's projection needs neither the boundary walk nor
-// the azimuth offsets.
-inline bool fast_projection(const IcpLaunch& a) { return a.dst.bins_exact && !a.dst.has_theta; }
+// the azimuth offsets, and its columns wrap by a mask (power-of-two width).
+inline bool fast_projection(const IcpLaunch& a) {
+  return a.dst.bins_exact && !a.dst.has_theta && a.dst.W > 0 && (a.dst.W & (a.dst.W - 1)) == 0;
+}
 
 template <bool R0, bool GATE, bool ASSOC, bool KAHAN, int T, bool ROWSTRIDE, bool FAST = false>
 cudaError_t launch_icp_ts(const IcpLaunch& a, long long blocks, cudaStream_t st) {

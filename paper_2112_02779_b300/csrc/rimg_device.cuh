@@ -80,8 +80,9 @@ __device__ __forceinline__ int wrap_col(float uc, int W) {
 // inside the vertical field of view; (u, v) are always valid indices and r is
 // the point's range from the receiver (|x - o| with the receiver offset o of
 // the last fixed-point step).  FAST: the caller knows that L's inverse table
-// is exact and that L has no azimuth offsets (theta_lut = 0), so the
-// projection is one straight-line block.
+// is exact, that L has no azimuth offsets (theta_lut = 0) and that its width
+// is a power of two, so the projection is one straight-line block and the
+// column wraps by a mask (floor(u_c + 1/2) mod W for every integer, NaN -> 0).
 template <bool R0, bool FAST = false>
 __device__ __forceinline__ bool project_px(const DevLevel& L, float3 x, int proj_iters, int& u, int& v,
                                            float& r) {
@@ -94,7 +95,7 @@ __device__ __forceinline__ bool project_px(const DevLevel& L, float3 x, int proj
     v = row_from_sin<FAST>(L, s);
     float uc = atan2_poly(x.y, x.x) * L.w_over_2pi;
     if (!FAST && L.has_theta) uc -= __ldg(L.thu + v);
-    u = wrap_col(uc, L.W);
+    u = FAST ? (__float2int_rd(uc + 0.5f) & (L.W - 1)) : wrap_col(uc, L.W);
   } else {
     // receiver-offset fixed point on the column angle 2 pi u_c / W
     float uc = atan2_poly(x.y, x.x) * L.w_over_2pi;
@@ -114,7 +115,7 @@ __device__ __forceinline__ bool project_px(const DevLevel& L, float3 x, int proj
       uc = atan2_poly(yp, xp) * L.w_over_2pi;
       if (!FAST && L.has_theta) uc -= __ldg(L.thu + v);
     }
-    u = wrap_col(uc, L.W);
+    u = FAST ? (__float2int_rd(uc + 0.5f) & (L.W - 1)) : wrap_col(uc, L.W);
   }
   return (s >= L.s_lo) && (s <= L.s_hi);   // false for NaN
 }

@@ -222,15 +222,17 @@ def test_icp_step_parity(R, name, levels, pose_kind):
 
 def _fast_projection(sens, level):
     """Whether the association kernels project into this level without the
-    boundary walk and the azimuth offsets (exact inverse table, theta_lut = 0)."""
+    boundary walk and the azimuth offsets, wrapping columns by a mask (exact
+    inverse table, theta_lut = 0, power-of-two width)."""
     L = sens.struct.level[level]
-    return bool(L.bins_exact) and not L.has_theta
+    return bool(L.bins_exact) and not L.has_theta and L.W > 0 and (L.W & (L.W - 1)) == 0
 
 
 def test_configs_cover_both_projection_forms(R):
     """The parity configurations reach the branch-free projection (exact
-    tables, no azimuth offsets) and the general one (azimuth offsets, or a
-    table uneven enough to need the boundary walk)."""
+    tables, no azimuth offsets, power-of-two widths) and the general one
+    (azimuth offsets, or a table uneven enough to need the boundary walk;
+    the ragged 24 x 48 case has a width that is not a power of two)."""
     forms = set()
     for name, levels in CFG_LEVELS:
         sens = gpu_sensor(R, CONFIGS[name].sensor(), levels)
