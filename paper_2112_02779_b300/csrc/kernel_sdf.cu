@@ -21,7 +21,10 @@ namespace {
 constexpr int kSdfThreads = 256;
 constexpr int kScanTile = 32;
 
-template <bool R0>
+// FAST: the level's inverse table is exact, it has no azimuth offsets and its
+// width is a power of two, so the projection takes its branch-free form (the
+// field-of-view and range tests stay branches: they skip a scan's work).
+template <bool R0, bool FAST>
 __global__ void __launch_bounds__(kSdfThreads) k_sdf(DevLevel L, int n_scans, const float* __restrict__ ranges,
                                                     const double* __restrict__ poses, int nx, int ny, long long n_vox,
                                                     float ox, float oy, float oz, float voxel, float trunc,
@@ -53,7 +56,7 @@ __global__ void __launch_bounds__(kSdfThreads) k_sdf(DevLevel L, int n_scans, co
                                     fmaf(c.x, cx, fmaf(c.y, cy, fmaf(c.z, cz, c.w))));
       int u, v;
       float r;
-      if (!project_px<R0>(L, xs, proj_iters, u, v, r)) continue;
+      if (!project_px<R0, FAST>(L, xs, proj_iters, u, v, r)) continue;
       const float meas = __ldg(ranges + (long long)(j0 + q) * img + (long long)v * L.W + u);
       if (!range_ok(meas)) continue;
       float d = meas - r;
@@ -81,12 +84,16 @@ cudaError_t launch_sdf(const DevLevel& L, int n_scans, const float* ranges, cons
   const long long n_vox = (long long)nx * ny * nz;
   if (n_vox == 0 || n_scans == 0) return cudaSuccess;
   const unsigned blocks = (unsigned)((n_vox + kSdfThreads - 1) / kSdfThreads);
-  if (L.r0 != 0.f)
-    k_sdf<true><<<blocks, kSdfThreads, 0, st>>>(L, n_scans, ranges, poses, nx, ny, n_vox, ox, oy, oz, voxel, trunc,
-                                                proj_iters, sdf, weight);
-  else
-    k_sdf<false><<<blocks, kSdfThreads, 0, st>>>(L, n_scans, ranges, poses, nx, ny, n_vox, ox, oy, oz, voxel, trunc,
-                                                 proj_iters, sdf, weight);
+  const bool fast = L.bins_exact && !L.has_theta && L.W > 0 && (L.W & (L.W - 1)) == 0;
+#define RIMG_SDF(R, F)                                                                                          \
+  k_sdf<R, F><<<blocks, kSdfThreads, 0, st>>>(L, n_scans, ranges, poses, nx, ny, n_vox, ox, oy, oz, voxel, trunc, \
+                                              proj_iters, sdf, weight)
+  if (L.r0 != 0.f) {
+    if (fast) RIMG_SDF(true, true); else RIMG_SDF(true, false);
+  } else {
+    if (fast) RIMG_SDF(false, true); else RIMG_SDF(false, false);
+  }
+#undef RIMG_SDF
   return cudaGetLastError();
 }
 
