@@ -345,8 +345,13 @@ def icp_terms(P_src, src_valid, T, dst_range, dst_n, dst_nvalid, phi_l, theta_l,
     weighted normal equations at pose T.
 
     Returns dict with H (6x6), g (6), sum_wr2, count, assoc (int64 index
-    v*W+u or -1 per source point), near_tie (bool per source point), and the
-    per-point residual e, weight w and Jacobian J (0 where not associated)."""
+    v*W+u or -1 per source point), near_tie (bool per source point), the
+    per-point residual e, weight w and Jacobian J (0 where not associated),
+    and the two distances the near-tie flag is read from: margin_u, the
+    distance of the continuous column u_c to the nearest half-integer (the
+    rounding boundary of the column choice, in pixels), and margin_row, the
+    distance of the elevation to the nearest row boundary or field-of-view
+    edge in units of the local row spacing (row_margin)."""
     P = np.asarray(P_src, np.float64).reshape(-1, 3)
     sv = np.asarray(src_valid, bool).reshape(-1)
     T = np.asarray(T, np.float64)
@@ -386,7 +391,7 @@ def icp_terms(P_src, src_valid, T, dst_range, dst_n, dst_nvalid, phi_l, theta_l,
         near |= sv & in_fov & (np.abs(dist - max_corr_dist) < 1e-5 * max_corr_dist)
     assoc = np.where(ok, v * Wd + u, -1)
     return dict(H=Hm, g=g, sum_wr2=float(np.sum(w * e * e)), count=int(ok.sum()),
-                assoc=assoc, near_tie=near, e=e, w=w, X=X, J=J)
+                assoc=assoc, near_tie=near, margin_u=m_u, margin_row=m_v, e=e, w=w, X=X, J=J)
 
 
 def pack29(terms):

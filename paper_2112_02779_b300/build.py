@@ -35,23 +35,39 @@ def up_to_date():
 
 def build(verbose=False, force=False, out=None, defines=()):
     """Compile every CUDA source into one shared library (default: the
-    in-tree librimg.so).  `defines` are extra -D tunables (e.g. RIMG_RING=2)."""
+    in-tree librimg.so).  `defines` are extra -D tunables (e.g. RIMG_RING=2).
+    Sources compile to objects in parallel, then one link step."""
     lib = out or LIB
     if not force and out is None and not defines and up_to_date():
         return LIB
     os.makedirs(os.path.dirname(lib), exist_ok=True)
-    tmp = lib + ".tmp"
-    cmd = [NVCC, "-O3", "-std=c++17", *ARCH, "-lineinfo", "-shared", "-Xcompiler", "-fPIC,-O2",
-           "-I", os.path.join(ROOT, "include"), "-o", tmp] + [f"-D{d}" for d in defines]
+    objdir = lib + ".objs"
+    os.makedirs(objdir, exist_ok=True)
+    common = [NVCC, "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC,-O2",
+              "-I", os.path.join(ROOT, "include")] + [f"-D{d}" for d in defines]
     if verbose:
-        cmd += ["-Xptxas", "-v"]
-    cmd += [os.path.join(CSRC, s) for s in SOURCES]
-    res = subprocess.run(cmd, capture_output=True, text=True)
+        common += ["-Xptxas", "-v"]
+
+    def compile_one(src):
+        obj = os.path.join(objdir, os.path.splitext(src)[0] + ".o")
+        res = subprocess.run(common + ["-c", "-o", obj, os.path.join(CSRC, src)], capture_output=True, text=True)
+        return src, obj, res
+
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 4)) as ex:
+        results = list(ex.map(compile_one, SOURCES))
+    failed = [r for r in results if r[2].returncode != 0]
+    for src, _, res in results:
+        if res.returncode != 0 or verbose:
+            sys.stderr.write(f"== {src}\n" + res.stdout + res.stderr)
+    if failed:
+        raise RuntimeError("nvcc failed building librimg.so: " + ", ".join(r[0] for r in failed))
+    tmp = lib + ".tmp"
+    res = subprocess.run([NVCC, *ARCH, "-shared", "-o", tmp] + [r[1] for r in results], capture_output=True,
+                         text=True)
     if res.returncode != 0:
         sys.stderr.write(res.stdout + res.stderr)
-        raise RuntimeError("nvcc failed building librimg.so")
-    if verbose:
-        sys.stderr.write(res.stderr)
+        raise RuntimeError("nvcc failed linking librimg.so")
     os.replace(tmp, lib)
     return lib
 
