@@ -256,7 +256,10 @@ int rimg_gn_update(int n_pairs, double* sums, double* pose, int* status, void* s
  *    batches return RIMG_ERR_WORKSPACE before anything is launched.
  *  - The first call on a device looks up the array's device address (with
  *    that device current) and caches it; make that first call before any
- *    stream capture.
+ *    stream capture.  The cached address lasts for the process: it does not
+ *    survive cudaDeviceReset or any other teardown of the device's primary
+ *    context, after which this entry point must not be called on that device
+ *    again.
  *  - All calls share the one array and it keeps the previous call's
  *    contents: the counters are cleared on `stream` before every kernel, but
  *    calls that overlap on the GPU (other streams, other host threads) race
@@ -267,6 +270,24 @@ int rimg_icp_step_static(const rimg_sensor* src, const rimg_sensor* dst, int lev
                          const float* src_range_l, const float* dst_planes_l, const float* dst_range_l,
                          double* pose, const rimg_params* p, int update, double* out29, int32_t* assoc,
                          int* status, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Initial pose by centre alignment (Section 4.1, problem statement: the
+ * rotation is typically initialised to the identity and the translation
+ * estimated by aligning the centres of the two point sets).  For each pair,
+ * with P_src / P_dst the valid pixels of the level-l images unprojected by
+ * Eq. 1-2 (src_range_l / dst_range_l: float32 [n][H_l][W_l] device, 16-byte
+ * aligned, of sensors src / dst at pyramid level `level`):
+ *   T_out[pair] = [I | mean(P_dst) - mean(P_src)]
+ * so that x = p + t maps the source centre onto the target centre.  Points are
+ * unprojected and summed in FP32 four pixels at a time, the sums carried in
+ * FP64.  T_out: float64 [n][16] device, row-major, overwritten (a valid
+ * T_init for rimg_register).  status (nullable): int32 [n] device;
+ * RIMG_FLAG_DEGENERATE is OR-ed in (and T_out = I) when either image has no
+ * valid pixel.  The two sensors may differ (each set uses its own tables).
+ * ------------------------------------------------------------------------- */
+int rimg_center_init(const rimg_sensor* src, const rimg_sensor* dst, int level, int n_pairs, const float* src_range_l,
+                     const float* dst_range_l, double* T_out, int* status, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Multi-scale registration (step A9), Section 4.1 with the coarse-to-fine

@@ -49,7 +49,7 @@ HEADER_FUNCTIONS = [
     "rimg_register_host_workspace_bytes", "rimg_register_host", "rimg_register_host_async",
     "rimg_gemm_bf16", "rimg_profile_begin", "rimg_profile_end", "rimg_sdf_integrate", "rimg_points_to_range",
     "rimg_cnn_param_count", "rimg_cnn_state_bytes", "rimg_cnn_workspace_bytes", "rimg_cnn_init", "rimg_cnn_load",
-    "rimg_propose", "rimg_cnn_grad", "rimg_cnn_train_step",
+    "rimg_propose", "rimg_cnn_grad", "rimg_cnn_train_step", "rimg_center_init",
 ]
 
 # Learned pose proposal constants (rimg.h)

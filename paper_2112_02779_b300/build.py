@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "librimg.so")
-SOURCES = ["rimg_api.cu", "kernels_prep.cu", "kernel_icp.cu", "rimg_noalloc.cu", "kernel_gemm.cu", "rimg_cnn.cu", "kernel_sdf.cu", "kernel_points.cu"]
+SOURCES = ["rimg_api.cu", "kernels_prep.cu", "kernel_icp.cu", "rimg_noalloc.cu", "kernel_gemm.cu", "rimg_cnn.cu", "kernel_sdf.cu", "kernel_points.cu", "kernel_center.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

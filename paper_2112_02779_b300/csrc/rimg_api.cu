@@ -685,6 +685,24 @@ int rimg_unproject(const rimg_sensor* s, int level, int n_images, const float* r
   return RIMG_OK;
 }
 
+int rimg_center_init(const rimg_sensor* src, const rimg_sensor* dst, int level, int n_pairs, const float* src_range_l,
+                     const float* dst_range_l, double* T_out, int* status, void* stream) {
+  int rc = check_sensor(src);
+  if (rc) return rc;
+  if ((rc = check_sensor(dst))) return rc;
+  if (level < 0 || level >= src->levels || level >= dst->levels || n_pairs < 0) return RIMG_ERR_INVALID_ARG;
+  if (n_pairs == 0) return RIMG_OK;
+  if (!src_range_l || !dst_range_l || !T_out) return RIMG_ERR_INVALID_ARG;
+  if ((reinterpret_cast<uintptr_t>(src_range_l) % 16) || (reinterpret_cast<uintptr_t>(dst_range_l) % 16) ||
+      (reinterpret_cast<uintptr_t>(T_out) % 8))
+    return RIMG_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = launch_center(dev_level(src, level), dev_level(dst, level), n_pairs, src_range_l, dst_range_l, T_out,
+                                status, st);
+  if (e != cudaSuccess) return cuda_fail(e, "centre kernel");
+  return RIMG_OK;
+}
+
 int rimg_sdf_integrate(const rimg_sensor* s, int level, int n_scans, const float* range_l,
                        const double* T_world_to_sensor, const rimg_grid* grid, float trunc, float* sdf,
                        float* weight, const rimg_params* p, void* stream) {

@@ -70,6 +70,9 @@ constexpr int kIcpItersMaxChunks = 4096;
 bool icp_iters_fits(int H, int W);
 cudaError_t launch_icp_iters(IcpLaunch a, int iters, cudaStream_t st);
 
+cudaError_t launch_center(const DevLevel& S, const DevLevel& D, int n_pairs, const float* src, const float* dst,
+                          double* T_out, int* status, cudaStream_t st);
+
 cudaError_t launch_sdf(const DevLevel& L, int n_scans, const float* ranges, const double* poses, int nx, int ny,
                        int nz, float ox, float oy, float oz, float voxel, float trunc, int proj_iters, float* sdf,
                        float* weight, cudaStream_t st);

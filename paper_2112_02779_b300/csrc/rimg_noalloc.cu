@@ -25,7 +25,8 @@ void* g_scratch_ptr[kMaxDevices] = {};
 
 // Device address of g_icp_scratch on the current device.  In host code the
 // symbol name is only a host-side stand-in, so the address is looked up once
-// per device (with that device current) and cached.
+// per device (with that device current) and cached for the life of the
+// process; a cudaDeviceReset would leave the cached address stale.
 int scratch_address(void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);

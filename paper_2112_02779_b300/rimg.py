@@ -78,6 +78,7 @@ _sig("rimg_cnn_train_step", _c_int, _vp, _c_size, _c_int, _c_int, _c_int, _c_int
      _P(rimg_adam), _c_int, _vp, _vp, _vp, _c_size, _vp)
 _sig("rimg_sdf_integrate", _c_int, _P(rimg_sensor), _c_int, _c_int, _vp, _vp, _P(rimg_grid), ctypes.c_float, _vp, _vp,
      _P(rimg_params), _vp)
+_sig("rimg_center_init", _c_int, _P(rimg_sensor), _P(rimg_sensor), _c_int, _c_int, _vp, _vp, _vp, _vp, _vp)
 _sig("rimg_points_to_range", _c_int, _P(rimg_sensor), _c_int, _c_int, _c_int, _vp, _vp, _vp, _vp, _P(rimg_params), _vp)
 _sig("rimg_profile_begin", _c_int, _c_int)
 _sig("rimg_profile_end", _c_int, _c_int, _P(_c_int), _P(_c_int), _P(_c_int), _P(ctypes.c_float), _P(ctypes.c_float))
@@ -348,6 +349,14 @@ def rimg_points_to_range(sensor, level, xyz, range_l, counts=None, T_cloud_to_se
     _check("rimg_points_to_range", _lib.rimg_points_to_range(
         sensor.ref(), level, n, m, _ptr(xyz), _ptr(counts), _ptr(T_cloud_to_sensor), _ptr(range_l),
         ctypes.byref(params) if params is not None else None, _stream(stream)))
+
+
+def rimg_center_init(src, dst, level, src_range_l, dst_range_l, T_out, status=None, stream=None):
+    """Initial poses [n, 16] = [I | centre of the target's valid points -
+    centre of the source's] from level-l range images [n, H_l, W_l]."""
+    n = src_range_l.shape[0] if src_range_l.dim() == 3 else 1
+    _check("rimg_center_init", _lib.rimg_center_init(src.ref(), dst.ref(), level, n, _ptr(src_range_l),
+                                                     _ptr(dst_range_l), _ptr(T_out), _ptr(status), _stream(stream)))
 
 
 # ---------------------------------------------------------------------------
