@@ -340,9 +340,15 @@ H21 = [(i, j) for i in range(6) for j in range(i, 6)]   # upper triangle, row-ma
 
 
 def icp_terms(P_src, src_valid, T, dst_range, dst_n, dst_nvalid, phi_l, theta_l, r0,
-              huber_delta, max_corr_dist=0.0, dst_n_margin=None):
+              huber_delta, max_corr_dist=0.0, dst_n_margin=None, assoc=None):
     """Associate every source point with the target image and build the
     weighted normal equations at pose T.
+
+    assoc (optional, int per source point, v*W+u or -1): use these
+    associations instead of deciding them by the projection (every other
+    step unchanged).  This isolates the arithmetic of a step from its
+    discrete decisions when checking an implementation that decided a few
+    near-tie pixels the other way.
 
     Returns dict with H (6x6), g (6), sum_wr2, count, assoc (int64 index
     v*W+u or -1 per source point), near_tie (bool per source point), the
@@ -359,6 +365,11 @@ def icp_terms(P_src, src_valid, T, dst_range, dst_n, dst_nvalid, phi_l, theta_l,
     Hh, Wd = dst_range.shape
     X = P @ R.T + t                                             # R_k p + t_k
     u, v, _, in_fov, det = project(X, phi_l, theta_l, r0, Wd, return_detail=True)   # Eq. 5
+    if assoc is not None:
+        a = np.asarray(assoc, np.int64).reshape(-1)
+        in_fov = a >= 0
+        v = np.where(in_fov, a // Wd, 0)
+        u = np.where(in_fov, a % Wd, 0)
     rq = np.asarray(dst_range, np.float64)[v, u]
     q = unproject_pixels(u, v, np.where(range_valid(rq), rq, 0.0), phi_l, theta_l, r0, Wd)  # Eq. 6
     n = np.asarray(dst_n, np.float64)[v, u]
@@ -531,6 +542,29 @@ def register(src_range, dst_range, src_sensor, dst_sensor, T_init, levels, iters
     if return_poses:
         return T, degenerate, poses
     return T, degenerate
+
+
+def center_align(P_src, P_dst):
+    """Initial pose of the registration problem (Section 4.1: the rotation
+    starts at the identity and the translation aligns the centres of the two
+    point sets): R = I, t = mean(P_dst) - mean(P_src), so that x = p + t maps
+    the source centre onto the target centre.  Either set empty: identity."""
+    P_src = np.asarray(P_src, np.float64).reshape(-1, 3)
+    P_dst = np.asarray(P_dst, np.float64).reshape(-1, 3)
+    T = np.eye(4)
+    if len(P_src) and len(P_dst):
+        T[:3, 3] = P_dst.mean(axis=0) - P_src.mean(axis=0)
+    return T
+
+
+def center_init(src_range, dst_range, src_sensor, dst_sensor, level=0):
+    """center_align of the valid points of two range images at pyramid level
+    l (Eq. 1-2 on the strided images, Section 4.1).  Sensors are (phi_lut,
+    theta_lut, r0) tuples.  Returns (T, ok); ok is False (T = I) when either
+    image has no valid pixel."""
+    P_s, v_s = source_points(src_range, *src_sensor, level)
+    P_d, v_d = source_points(dst_range, *dst_sensor, level)
+    return center_align(P_s[v_s], P_d[v_d]), bool(v_s.any() and v_d.any())
 
 
 def pose_error(T, T_ref):
