@@ -202,20 +202,21 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
 // The 29 reduced quantities live in 15 float2 accumulators (30 lanes):
-// lane index f = 2 * pair + (0 for .x, 1 for .y).  Pairs 0..8 are updated by
+// lane index f = 2 * pair + (0 for .x, 1 for .y).  Pairs 0..11 are updated by
 // packed FP32x2 FMAs whose operands are register pairs that arise without
 // moves -- (a0, a1) and (a2, e) as computed, (nx, ny) as loaded -- plus the
-// swaps (ny, nx) and (e, a2); pairs 9..13 hold scalar FMAs, pair 14 the count.
-// kFlat maps the output order (21 upper-triangle J^T W J entries row-major,
-// 6 J^T W e, sum w e^2, count) to lanes.
+// swaps (ny, nx) and (e, a2) and the broadcast (nz, nz); pairs 12 and 13 hold
+// scalar FMAs, pair 14 the count.  kFlat maps the output order (21
+// upper-triangle J^T W J entries row-major, 6 J^T W e, sum w e^2, count) to
+// lanes.
 constexpr int kPairs = 15;
-__constant__ int kFlat[kRed] = {0,  18, 2,  4,  6,  19,  // H00..H05
-                                1,  9,  7,  5,  20,      // H11..H15
-                                10, 12, 14, 21,          // H22..H25
-                                16, 22, 23,              // H33..H35
-                                17, 24,                  // H44, H45
-                                25,                      // H55
-                                8,  3,  26, 15, 13, 27,  // g0..g5
+__constant__ int kFlat[kRed] = {0,  24, 2,  4,  6,  18,  // H00..H05
+                                1,  9,  7,  5,  19,      // H11..H15
+                                10, 12, 14, 20,          // H22..H25
+                                16, 25, 22,              // H33..H35
+                                17, 23,                  // H44, H45
+                                26,                      // H55
+                                8,  3,  27, 15, 13, 21,  // g0..g5
                                 11, 28};                 // sum w e^2, count
 
 // Point-to-plane terms of one association: residual e = n.x - d, IRLS weight,
@@ -231,10 +232,9 @@ __device__ __forceinline__ void accumulate_px(float2 (&t)[kPairs], float x, floa
   const float w = inv_delta > 0.f ? rsqrtf(fmaf(q, q, 1.f)) : 1.f;
   const float a0 = fmaf(y, nz, -z * ny), a1 = fmaf(z, nx, -x * nz), a2 = fmaf(x, ny, -y * nx);
   const float2 P1 = f2(a0, a1), P2 = f2(a2, e), N1 = f2(nx, ny);
-  const float2 M1 = f2(ny, nx), S2 = f2(e, a2);
+  const float2 M1 = f2(ny, nx), S2 = f2(e, a2), Z2 = f2(nz, nz);
   const float2 W2 = f2(w, w);
   const float2 UP1 = mul2(W2, P1), UP2 = mul2(W2, P2), UN1 = mul2(W2, N1);
-  const float wnz = w * nz;
   t[0] = fma2(UP1, P1, t[0]);                          // H00 H11
   t[1] = fma2(UP1, P2, t[1]);                          // H02 g1
   t[2] = fma2(UP1, N1, t[2]);                          // H03 H14
@@ -244,16 +244,13 @@ __device__ __forceinline__ void accumulate_px(float2 (&t)[kPairs], float x, floa
   t[6] = fma2(UP2, N1, t[6]);                          // H23 g4
   t[7] = fma2(UP2, M1, t[7]);                          // H24 g3
   t[8] = fma2(UN1, N1, t[8]);                          // H33 H44
-  t[9].x = fmaf(UP1.x, a1, t[9].x);                    // H01
-  t[9].y = fmaf(UP1.x, nz, t[9].y);                    // H05
-  t[10].x = fmaf(UP1.y, nz, t[10].x);                  // H15
-  t[10].y = fmaf(UP2.x, nz, t[10].y);                  // H25
-  t[11].x = fmaf(UN1.x, ny, t[11].x);                  // H34
-  t[11].y = fmaf(UN1.x, nz, t[11].y);                  // H35
-  t[12].x = fmaf(UN1.y, nz, t[12].x);                  // H45
-  t[12].y = fmaf(wnz, nz, t[12].y);                    // H55
-  t[13].x = fmaf(UP2.x, e, t[13].x);                   // g2
-  t[13].y = fmaf(wnz, e, t[13].y);                     // g5
+  t[9] = fma2(UP1, Z2, t[9]);                          // H05 H15
+  t[10] = fma2(UP2, Z2, t[10]);                        // H25 g5
+  t[11] = fma2(UN1, Z2, t[11]);                        // H35 H45
+  t[12].x = fmaf(UP1.x, a1, t[12].x);                  // H01
+  t[12].y = fmaf(UN1.x, ny, t[12].y);                  // H34
+  t[13].x = fmaf(w * nz, nz, t[13].x);                 // H55
+  t[13].y = fmaf(UP2.x, e, t[13].y);                   // g2
   // an association counts when its plane is not the all-zero invalid plane
   // (stored as +0.f; a unit normal has a non-zero component)
   t[14].x += (__float_as_uint(nx) | __float_as_uint(ny) | __float_as_uint(nz)) ? 1.f : 0.f;
