@@ -30,8 +30,9 @@ def R():
 
 def _sequence(cfg_name, n_scans, seed):
     """n_scans range images of one outdoor scene from a sensor moving along x
-    with small yaw changes; returns (sensor, images [n,H,W], world poses)."""
-    cfg = CONFIGS[cfg_name]
+    with small yaw changes; returns (sensor, images [n,H,W], world poses).
+    cfg_name: a workload name or a PairConfig."""
+    cfg = CONFIGS[cfg_name] if isinstance(cfg_name, str) else cfg_name
     sensor = cfg.sensor()
     rng = np.random.default_rng(seed)
     poses = []
@@ -59,10 +60,26 @@ def _check(sdf_g, w_g, sdf_o, w_o, near, X, T_ws, n_scans):
     assert both.sum() > 1000
 
 
+def _r0_fast_config():
+    """The 32 x 512 sensor (uniform elevations, theta_lut = 0, power-of-two
+    width, so an exact inverse table) with a receiver offset r0 = 1.5 cm: the
+    branch-free projection inside the receiver-offset fixed point."""
+    import dataclasses
+    return dataclasses.replace(CONFIGS["pair32x512"], name="pair32x512_r0", config_id=91, r0=0.015)
+
+
 @pytest.mark.parametrize("cfg_name,level,trunc", [("pair64x1024", 0, 0.5), ("pair64x1024", 1, 0.0),
-                                                   ("lut64x512", 0, 0.3)])
+                                                   ("lut64x512", 0, 0.3), ("r0_fast", 0, 0.3),
+                                                   ("r0_fast", 1, 0.0)])
 def test_sdf_matches_oracle(R, cfg_name, level, trunc):
     n = 6
+    if cfg_name == "r0_fast":
+        cfg_name = _r0_fast_config()
+        s0 = cfg_name.sensor()
+        sens0 = R.rimg_sensor_build(s0.H, s0.W, 2, s0.phi_lut, s0.theta_lut, s0.r0)
+        L = sens0.struct.level[level]
+        # the launch takes the branch-free form: exact table, no azimuth offsets, power-of-two width
+        assert L.bins_exact and not L.has_theta and (L.W & (L.W - 1)) == 0 and s0.r0 > 0
     sensor, imgs, poses = _sequence(cfg_name, n, seed=11)
     T_ws = [np.linalg.inv(W) for W in poses]
     dims, origin, voxel = (64, 48, 16), (-6.0, -6.0, -0.5), 0.25
