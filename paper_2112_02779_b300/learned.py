@@ -191,10 +191,24 @@ def summarize(err_r, err_t):
             "p95_trans_m": float(np.quantile(err_t, 0.95))}
 
 
-def evaluate(R, net, reg, test, schedules, tau, timing_pairs=4096, log=print):
+# plain schedules of the ablation beside the proposal's own schedules: fewer
+# iterations on every level, or on the coarse levels only
+PLAIN_ABLATION = [(10, 8, 8, 8), (10, 6, 6, 6), (10, 5, 5, 5), (10, 10, 10, 5), (8, 8, 8, 8), (6, 6, 6, 6),
+                  (5, 5, 5, 5), (5, 10, 10, 10)]
+MATCH_SUCCESS = 0.005     # two pipelines count as equally accurate when their success rates differ by less
+
+
+def evaluate(R, net, reg, test, schedules, tau, timing_pairs=4096, log=print, plain_schedules=None):
     """Plain (identity start, full schedule) against proposal + each schedule
     with the convergence judge (last step above tau = (rad, m): rejected) and
-    the plain fallback."""
+    the plain fallback.
+
+    Ablation: the plain method from the identity is also run at every
+    schedule of `schedules` and of `plain_schedules`, so that a gain is
+    claimed only against the fastest plain schedule that is as accurate:
+    each proposal entry gets `matched_plain`, the fastest plain run whose
+    success rate is at least the entry's minus MATCH_SUCCESS, and
+    `gain_vs_matched` = its pairs/s over that run's."""
     torch = _torch()
     cfg = reg.cfg
     src, dst = test["src"], test["dst"]
@@ -214,6 +228,18 @@ def evaluate(R, net, reg, test, schedules, tau, timing_pairs=4096, log=print):
     s_m, d_m, e_m = src[:m], dst[:m], eye[:m]
     t_plain = _timed(lambda: reg(s_m, d_m, e_m, full))
     res["plain"]["pairs_per_s"] = m / t_plain
+    # the ablation: plain from the identity at every schedule
+    res["plain_schedules"] = [dict(res["plain"], iters=list(full))]
+    seen = {tuple(full)}
+    for sched in list(schedules) + list(plain_schedules or []):
+        if tuple(sched) in seen:
+            continue
+        seen.add(tuple(sched))
+        T_p = reg(src, dst, eye, sched).cpu().numpy()
+        entry = {"iters": list(sched), **summarize(*pose_errors(T_p, label))}
+        entry["pairs_per_s"] = m / _timed(lambda: reg(s_m, d_m, e_m, sched))
+        res["plain_schedules"].append(entry)
+        log(f"  plain {sched}: success {entry['success']:.4f}, {entry['pairs_per_s']:.0f} pairs/s")
     res["learned"] = []
     for sched in schedules:
         T_l, s32 = reg(src, dst, T0, sched, fitness=True)
@@ -241,10 +267,21 @@ def evaluate(R, net, reg, test, schedules, tau, timing_pairs=4096, log=print):
 
         t_l = _timed(pipeline)
         entry["pairs_per_s"] = m / t_l
+        same = [p for p in res["plain_schedules"] if p["success"] >= entry["judged"]["success"] - MATCH_SUCCESS]
+        if same:
+            best = max(same, key=lambda p: p["pairs_per_s"])
+            entry["matched_plain"] = {"iters": best["iters"], "success": best["success"],
+                                      "pairs_per_s": best["pairs_per_s"]}
+            entry["gain_vs_matched"] = entry["pairs_per_s"] / best["pairs_per_s"]
+        else:
+            entry["matched_plain"] = None            # more accurate than every plain schedule
+            entry["gain_vs_matched"] = None
         res["learned"].append(entry)
+        mp = entry["matched_plain"]
         log(f"  sched {sched}: success {entry['judged']['success']:.4f} (no judge {entry['no_judge']['success']:.4f}),"
             f" rejected {entry['rejected']:.4f}, {entry['pairs_per_s']:.0f} pairs/s"
-            f" (plain {res['plain']['success']:.4f}, {res['plain']['pairs_per_s']:.0f} pairs/s)")
+            f" (plain {res['plain']['success']:.4f}, {res['plain']['pairs_per_s']:.0f} pairs/s; fastest plain as"
+            f" accurate: {mp['iters'] if mp else None}, gain {entry['gain_vs_matched']})")
     return res
 
 
@@ -298,7 +335,8 @@ def main(argv=None):
         (2, 8, 8, 8), (2, 7, 7, 7), (2, 6, 6, 6), (2, 5, 5, 5), (2, 3, 3, 3), (2, 10, 10, 5), (2, 5, 5, 8),
         (2, 3, 3, 8)]
     schedules = [s[:L] for s in schedules]
-    report["eval"] = evaluate(R, net, reg, test_set, schedules, tau)
+    plain_extra = [s[:L] for s in PLAIN_ABLATION]
+    report["eval"] = evaluate(R, net, reg, test_set, schedules, tau, plain_schedules=plain_extra)
     if a.save:
         np.save(a.save, net.params.cpu().numpy())
     if a.out:

@@ -1,6 +1,6 @@
-"""Host-side logic of bench.py, on the CPU: the pose check that reads the
-GPU-vs-oracle differences with the oracle's own end-of-schedule motion, and
-the committed ncu summaries it takes traffic and instruction counts from."""
+"""Host-side logic of bench.py, on the CPU: the summary of the per-level
+GPU-vs-oracle pose check, and the committed ncu summaries it takes traffic
+and instruction counts from."""
 import importlib.util
 import os
 import re
@@ -17,26 +17,20 @@ def _bench():
     return b
 
 
-def test_pose_check_reads_settled_and_moving_pairs():
+def test_pose_check_summarises_the_per_level_report():
     b = _bench()
-    # pair 0: settled, within the bar; pair 1: moving (last 2e-4 / 3e-4, previous 3e-4 / 4e-4),
-    # beyond 1e-4 but inside 1e-4 + 3 x tail; pair 2: moving, within 1e-4
-    err = [(1e-6, 2e-6), (2e-4, 3e-4), (5e-5, 1e-5)]
-    last = [(1e-6, 1e-6), (2e-4, 3e-4), (1e-4, 1e-4)]
-    prev = [(2e-6, 2e-6), (3e-4, 4e-4), (1e-4, 1e-4)]
-    r = b.pose_check(err, last, prev)
-    assert r["pairs"] == 3 and r["within_1e-4"] == 2 and r["settled_pairs"] == 1
-    assert r["settled_within_1e-4"] and r["beyond_1e-4_all_unsettled_within_tail_bar"]
-    assert r["max_err_settled"] == [1e-6, 2e-6]
-    # a settled pair beyond the bar fails the check
-    r = b.pose_check([(2e-4, 0.0)], [(1e-6, 1e-6)], [(1e-6, 1e-6)])
-    assert not r["settled_within_1e-4"] and not r["beyond_1e-4_all_unsettled_within_tail_bar"]
-    # a moving pair beyond its tail bar fails it too: last 1e-5, previous 1e-4 -> rho 0.1,
-    # tail = max(last, last rho / (1 - rho)) = 1e-5, bar 1.3e-4
-    r = b.pose_check([(2e-4, 0.0)], [(1e-5, 1e-4)], [(1e-4, 1e-4)])
-    assert not r["beyond_1e-4_all_unsettled_within_tail_bar"]
-    r = b.pose_check([(1.25e-4, 0.0)], [(1e-5, 1e-4)], [(1e-4, 1e-4)])
-    assert r["beyond_1e-4_all_unsettled_within_tail_bar"]
+    rep = {"pairs": 3, "levels_checked": 12, "max_err": [2e-4, 3e-4], "explained": 1, "unexplained": 1,
+           "beyond": [dict(pair=1, level_index=3, err=[2e-4, 3e-4], split=4, split_ties=2, split_off_tie=0,
+                           step_err_given_max=[1e-7, 2e-7], explained=True),
+                      dict(pair=2, level_index=2, err=[1e-4, 1.5e-4], split=None, split_ties=0, split_off_tie=0,
+                           step_err_given_max=[1e-3, 1e-3], explained=False)]}
+    whole = [(1e-6, 2e-6), (2e-4, 3e-4), (5e-5, 1e-5)]
+    r = b.pose_check(rep, whole)
+    assert r["pairs"] == 3 and r["levels_checked"] == 12 and r["levels_within_1e-4"] == 10
+    assert r["levels_beyond_1e-4_explained"] == 1 and r["levels_beyond_1e-4_unexplained"] == 1
+    assert r["whole_registration_within_1e-4"] == 2
+    assert r["whole_registration_median_err"] == [5e-5, 1e-5]
+    assert [x["pair"] for x in r["beyond"]] == [1, 2]
 
 
 def test_committed_profiles_carry_the_keys_bench_reads():
