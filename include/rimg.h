@@ -329,11 +329,22 @@ int rimg_register_last_sums(const rimg_sensor* src, const rimg_sensor* dst, int 
  * call.  Every group splits into params->streams sub-batches of >= 32 pairs;
  * all sub-batches of all groups are spread over eight internal streams
  * (largest first, to the least-loaded stream) forked from and joined back
- * into `stream`, so the groups run concurrently.  The call queues work only
- * (no synchronisation, no allocation) and can be captured in a CUDA graph
- * once the library has been used on the device (the first call creates the
- * internal streams and events).  Semantics per group are those of
- * rimg_register.  workspace: device, 256-byte aligned, >=
+ * into `stream`, so the groups run concurrently.
+ *
+ * The leading small levels of the schedule (the coarsest levels whose pair
+ * fits one 256-thread block, when the target projects with the branch-free
+ * form and no distance gate is set) of all groups run in ONE persistent
+ * launch per kernel form (receiver offset or not, Kahan or not): its blocks
+ * take pairs from an atomic work queue ordered by cost, largest groups
+ * first, and run each pair's queued levels with all their iterations and
+ * FP64 updates; no block waits for another.  The finer levels then run per
+ * sub-batch on the internal streams.  rimg_autotune may move a level out of
+ * the queue (per-iteration launches) where that measured faster.
+ *
+ * The call queues work only (no synchronisation, no allocation) and can be
+ * captured in a CUDA graph once the library has been used on the device (the
+ * first call creates the internal streams and events).  Semantics per group
+ * are those of rimg_register.  workspace: device, 256-byte aligned, >=
  * rimg_register_groups_workspace_bytes().
  * ------------------------------------------------------------------------- */
 typedef struct rimg_group {
@@ -354,14 +365,21 @@ int rimg_register_groups_workspace_bytes(int n_groups, const rimg_group* groups,
 int rimg_register_groups(int n_groups, const rimg_group* groups, void* workspace, size_t workspace_bytes,
                          void* stream);
 
-/* Autotuner for the association kernel's launch shape (threads per block and
- * blocks per pair, i.e. rows per block) at every level of every group, for
- * the sub-batch sizes rimg_register_groups will use.  It builds each group's
- * pyramids in the workspace, times every candidate shape on the group's own
- * data (without updating poses; T_out receives a copy of T_init) and keeps
- * the fastest in a process-wide table that later launches of the same
- * (level size, pairs) use.  SYNCHRONOUS; returns the number of entries set
- * (>= 0) or a negative status.  rimg_autotune_clear empties the table. */
+/* Autotuner of the per-level schedule and launch shapes, for the sub-batch
+ * sizes rimg_register_groups will use.  It builds each group's pyramids in the
+ * workspace and, on the group's own data, for every level:
+ *  - times every candidate shape of the association kernel (threads per
+ *    block, blocks per pair) without updating poses;
+ *  - where the level's pair fits one block, times its whole iteration count
+ *    both ways -- all iterations in one block per pair (the persistent queue
+ *    of rimg_register_groups / the one-launch level of rimg_register) and one
+ *    association launch of the best shape plus one FP64 solve launch per
+ *    iteration -- and records the faster schedule;
+ *  - records the best shape for levels that run as per-iteration launches.
+ * The choices go to a process-wide table keyed by (level size, pairs) that
+ * later rimg_register / rimg_register_groups calls use.  T_out ends as a copy
+ * of T_init.  SYNCHRONOUS; returns the number of entries set (>= 0) or a
+ * negative status.  rimg_autotune_clear empties the table. */
 int rimg_autotune(int n_groups, const rimg_group* groups, void* workspace, size_t workspace_bytes, void* stream);
 int rimg_autotune_clear(void);
 
@@ -562,8 +580,9 @@ int rimg_cnn_train_step(void* state, size_t state_bytes, int n, int H, int W, in
  * Kernel ids: 0 unproject, 1 pyramid, 2 normals (+ plane pyramid),
  * 3 icp step (association + reduction), 4 source-range pyramid, 5 FP64
  * solve + pose update, 6 SDF integration, 7 point-cloud projection, 8 all
- * iterations of a small pyramid level (one block per pair).  Not for use
- * during stream capture.
+ * iterations of a small pyramid level (one block per pair), 9 the persistent
+ * small-level queue of rimg_register_groups (level -1, n_pairs = items).  Not
+ * for use during stream capture.
  * ------------------------------------------------------------------------- */
 int rimg_profile_begin(int max_launches);
 int rimg_profile_end(int cap, int* kernel_id, int* level, int* n_pairs, float* start_ms, float* ms);

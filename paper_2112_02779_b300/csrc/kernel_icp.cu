@@ -7,6 +7,7 @@
 // counter, no spinning; the last block of a pair sums the block records in
 // FP64).  k_solve then solves the 6x6 system in FP64 and composes the SE(3)
 // update, one warp per pair.
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -652,6 +653,145 @@ __global__ void __launch_bounds__(THREADS, RIMG_ICP_THREADS_PER_SM / THREADS) k_
   if (tid == 0 && degenerate && a.status) a.status[pair] |= RIMG_FLAG_DEGENERATE;
 }
 
+// ---------------------------------------------------------------------------
+// Persistent work queue over the small levels of uneven batches.
+
+// Copies one group descriptor (a kernel parameter) into device memory, so
+// that the descriptor table is written inside the stream (and a captured
+// graph carries it).
+__global__ void k_put_group(QueueGroup g, QueueGroup* dst) {
+  static_assert(sizeof(QueueGroup) % 4 == 0, "descriptor copied as words");
+  const int* s = reinterpret_cast<const int*>(&g);
+  int* d = reinterpret_cast<int*>(dst);
+  for (int i = threadIdx.x; i < (int)(sizeof(QueueGroup) / 4); i += blockDim.x) d[i] = s[i];
+}
+
+// One block per item at a time: the block takes the next item from the
+// counter, runs the item's pair through all its group's queued levels
+// (association + reduction of the whole level, the FP64 update by the first
+// warp, next iteration) and goes on to the next item.  Items are ordered by
+// cost (the host lists the most expensive groups first).  No block waits for
+// another; the last blocks to find the queue empty simply exit.
+template <bool R0, bool KAHAN>
+__global__ void __launch_bounds__(kQueueThreads, RIMG_ICP_THREADS_PER_SM / kQueueThreads)
+    k_icp_queue(const QueueGroup* __restrict__ groups, int n_groups, int n_items, unsigned* counter) {
+  constexpr int THREADS = kQueueThreads;
+  constexpr int kDL = (int)(sizeof(DevLevel) / 4);
+  static_assert(sizeof(DevLevel) % 4 == 0 && kDL <= 32, "a level view is copied by one warp");
+  extern __shared__ float4 smem_raw[];
+  IcpSmem<THREADS>& sm = *reinterpret_cast<IcpSmem<THREADS>*>(smem_raw);
+  __shared__ IcpLaunch la;
+  __shared__ double Tp[12];
+  __shared__ int item_s, group_s, iters_s, degenerate;
+  const int tid = threadIdx.x;
+  while (true) {
+    if (tid == 0) {
+      const int it = (int)atomicAdd(counter, 1u);
+      int g = 0;
+      while (g + 1 < n_groups && it >= groups[g + 1].item0) ++g;
+      item_s = it;
+      group_s = g;
+      degenerate = 0;
+    }
+    __syncthreads();
+    const int item = item_s;
+    if (item >= n_items) break;
+    const QueueGroup* G = groups + group_s;
+    const int pair = item - G->item0;
+    if (tid < 12) {
+      Tp[tid] = G->pose[(long long)pair * 16 + tid];
+      reinterpret_cast<float*>(sm.T4)[tid] = (float)Tp[tid];
+    }
+    const int nl = G->n_lvl;
+    bool ran = false;
+    for (int k = 0; k < nl; ++k) {
+      __syncthreads();                       // the previous level's readers of `la` are done
+      const QueueLevel& QL = G->lvl[k];
+      if (tid < kDL) {
+        reinterpret_cast<int*>(&la.src)[tid] = reinterpret_cast<const int*>(&QL.src)[tid];
+      } else if (tid >= 32 && tid < 32 + kDL) {
+        reinterpret_cast<int*>(&la.dst)[tid - 32] = reinterpret_cast<const int*>(&QL.dst)[tid - 32];
+      } else if (tid == 64) {
+        la.src_range = QL.src_range;
+        la.dst_planes = QL.planes;
+        la.dst_range = nullptr;
+        la.out29 = nullptr;
+        la.assoc = nullptr;
+        la.huber_delta = G->huber_delta;
+        la.max_corr_dist = 0.f;
+        la.proj_iters = G->proj_iters;
+        la.kahan = KAHAN ? 1 : 0;
+        la.n_pairs = G->n_pairs;
+        iters_s = QL.iters;
+      }
+      __syncthreads();
+      const int iters = iters_s;
+      for (int it = 0; it < iters; ++it) {
+        icp_block_terms<R0, false, false, KAHAN, THREADS, true, true>(la, sm, pair, 0, la.src.H);
+        if (tid < kRed) sm.tot[tid] = (double)block_total<THREADS>(sm, tid);
+        __syncthreads();
+        if (tid < 32) {
+          const bool last = (k == nl - 1) && (it == iters - 1);
+          const bool ok = warp_gn_update(sm.tot, Tp, reinterpret_cast<float*>(sm.T4), last ? sm.tot + 29 : nullptr,
+                                         tid);
+          if (!ok && tid == 0) degenerate = 1;
+        }
+        __syncthreads();
+        ran = true;
+      }
+    }
+    if (tid < 12) G->pose[(long long)pair * 16 + tid] = Tp[tid];
+    if (ran && tid < kRedStride && G->sums) G->sums[(long long)pair * kRedStride + tid] = sm.tot[tid];
+    if (tid == 0 && degenerate && G->status) G->status[pair] |= RIMG_FLAG_DEGENERATE;
+    __syncthreads();                         // before item_s is overwritten
+  }
+}
+
+bool queue_level_ok(int H, int W) {
+  const int cpr = W / 4;
+  return icp_iters_fits(H, W) && cpr > 0 && cpr <= kQueueThreads && kQueueThreads % cpr == 0;
+}
+
+namespace {
+template <bool R0, bool KAHAN>
+cudaError_t launch_queue_t(const QueueGroup* dev_groups, int n_groups, int n_items, unsigned* counter,
+                           cudaStream_t st) {
+  constexpr size_t bytes = sizeof(IcpSmem<kQueueThreads>);
+  static int grid_cap = 0;     // resident blocks on the device (per instantiation)
+  if (grid_cap == 0) {
+    cudaError_t e = cudaFuncSetAttribute(k_icp_queue<R0, KAHAN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)bytes);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_icp_queue<R0, KAHAN>, kQueueThreads, bytes);
+    grid_cap = std::max(1, sms) * std::max(1, occ);
+  }
+  const int grid = std::min(n_items, grid_cap);
+  k_icp_queue<R0, KAHAN><<<grid, kQueueThreads, bytes, st>>>(dev_groups, n_groups, n_items, counter);
+  return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_icp_queue(const QueueGroup* host_groups, int n_groups, QueueGroup* dev_groups, unsigned* counter,
+                             bool r0, bool kahan, cudaStream_t st) {
+  int n_items = 0;
+  for (int g = 0; g < n_groups; ++g) n_items += host_groups[g].n_pairs;
+  if (n_items == 0) return cudaSuccess;
+  for (int g = 0; g < n_groups; ++g) {
+    k_put_group<<<1, 64, 0, st>>>(host_groups[g], dev_groups + g);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  if (r0) return kahan ? launch_queue_t<true, true>(dev_groups, n_groups, n_items, counter, st)
+                       : launch_queue_t<true, false>(dev_groups, n_groups, n_items, counter, st);
+  return kahan ? launch_queue_t<false, true>(dev_groups, n_groups, n_items, counter, st)
+               : launch_queue_t<false, false>(dev_groups, n_groups, n_items, counter, st);
+}
+
 cudaError_t launch_solve(int n_pairs, double* sums, double* pose, int* status, cudaStream_t st) {
   if (n_pairs == 0) return cudaSuccess;
   k_solve<<<(n_pairs + 3) / 4, 128, 0, st>>>(n_pairs, sums, pose, status);
@@ -677,6 +817,10 @@ namespace {
 // Launch shapes chosen by rimg_autotune, keyed by (level rows, columns, pairs).
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int>, std::pair<int, int>> g_tune;
+// Per-level schedule chosen by rimg_autotune for levels that fit one block:
+// true = all iterations in one block per pair (k_icp_iters / the queue),
+// false = one multi-block association launch plus one solve per iteration.
+std::map<std::tuple<int, int, int>, bool> g_sched;
 }  // namespace
 
 void icp_tune_set(int H, int W, int n_pairs, int threads, int bpp) {
@@ -687,11 +831,29 @@ void icp_tune_set(int H, int W, int n_pairs, int threads, int bpp) {
 void icp_tune_clear() {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune.clear();
+  g_sched.clear();
+}
+
+void icp_tune_erase(int H, int W, int n_pairs) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune.erase(std::make_tuple(H, W, n_pairs));
+}
+
+void icp_sched_set(int H, int W, int n_pairs, bool fused) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_sched[std::make_tuple(H, W, n_pairs)] = fused;
+}
+
+bool icp_sched_fused(int H, int W, int n_pairs) {
+  if (!icp_iters_fits(H, W)) return false;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_sched.find(std::make_tuple(H, W, n_pairs));
+  return it == g_sched.end() ? true : it->second;
 }
 
 int icp_tune_size() {
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  return (int)g_tune.size();
+  return (int)(g_tune.size() + g_sched.size());
 }
 
 void icp_grid(int H, int W, int n_pairs, int* bpp, int* rows_per_block, int* threads) {
@@ -765,10 +927,12 @@ cudaError_t launch_icp_ts(const IcpLaunch& a, long long blocks, cudaStream_t st)
 template <bool R0, bool GATE, bool ASSOC, bool KAHAN, int T>
 cudaError_t launch_icp_t(const IcpLaunch& a, long long blocks, cudaStream_t st) {
   if constexpr (!GATE && !ASSOC) {
+    const bool fast = fast_projection(a);
     if (row_stride(a, T)) {
-      if (fast_projection(a)) return launch_icp_ts<R0, GATE, ASSOC, KAHAN, T, true, true>(a, blocks, st);
+      if (fast) return launch_icp_ts<R0, GATE, ASSOC, KAHAN, T, true, true>(a, blocks, st);
       return launch_icp_ts<R0, GATE, ASSOC, KAHAN, T, true>(a, blocks, st);
     }
+    if (fast) return launch_icp_ts<R0, GATE, ASSOC, KAHAN, T, false, true>(a, blocks, st);
   }
   return launch_icp_ts<R0, GATE, ASSOC, KAHAN, T, false>(a, blocks, st);
 }

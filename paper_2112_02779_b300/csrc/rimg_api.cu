@@ -321,45 +321,68 @@ int prep_slice(const rimg_sensor* src, const rimg_sensor* dst, int n, const floa
   return RIMG_OK;
 }
 
-// Registration of the pairs [p0, p0 + n) of a batch on one stream; every
-// buffer is addressed through the per-pair offsets of that range.
-int register_slice(const rimg_sensor* src, const rimg_sensor* dst, int p0, int n, const float* src_range,
-                   const float* dst_range, const double* T_init, double* T_out, int levels, const int* iters,
-                   const rimg_params* p, int* status, char* ws, const RegWs& R, cudaStream_t st) {
+// The pairs [p0, p0 + n) of a batch: status cleared, T_out initialised, the
+// completion counters zeroed and the pyramids built, on one stream.
+int slice_begin(const rimg_sensor* src, const rimg_sensor* dst, int p0, int n, const float* src_range,
+                const float* dst_range, const double* T_init, double* T_out, int levels, const rimg_params* p,
+                int* status, char* ws, const RegWs& R, cudaStream_t st) {
   const int H = src->H, W = src->W;
   const size_t N = (size_t)H * W;
   src_range += p0 * N;
   dst_range += p0 * N;
   T_init += 16 * (size_t)p0;
   T_out += 16 * (size_t)p0;
-  if (status) status += p0;
-  if (status) RIMG_CUDA(cudaMemsetAsync(status, 0, sizeof(int) * n, st));
+  if (status) RIMG_CUDA(cudaMemsetAsync(status + p0, 0, sizeof(int) * n, st));
   if (T_out != T_init)
     RIMG_CUDA(cudaMemcpyAsync(T_out, T_init, sizeof(double) * 16 * n, cudaMemcpyDeviceToDevice, st));
   const IcpScratch scr = icp_scratch(ws, R.icp, H, p0);
   RIMG_CUDA(cudaMemsetAsync(scr.counters, 0, sizeof(unsigned) * n, st));
   const SliceBufs b = slice_bufs(ws, R, H, W, levels, p0);
-  int rc0 = prep_slice(src, dst, n, src_range, dst_range, levels, p, b, st);
-  if (rc0) return rc0;
+  return prep_slice(src, dst, n, src_range, dst_range, levels, p, b, st);
+}
+
+// Gauss-Newton steps of the schedule levels k >= k_first for the pairs
+// [p0, p0 + n) (after slice_begin): a level whose pair fits one block runs all
+// its iterations in one launch unless the autotuner chose per-iteration
+// launches for it; other levels run one association and one solve launch per
+// iteration.
+int slice_levels(const rimg_sensor* src, const rimg_sensor* dst, int p0, int n, const float* src_range,
+                 const float* dst_range, double* T_out, int levels, const int* iters, const rimg_params* p,
+                 int* status, char* ws, const RegWs& R, int k_first, cudaStream_t st) {
+  const int H = src->H, W = src->W;
+  const size_t N = (size_t)H * W;
+  src_range += p0 * N;
+  dst_range += p0 * N;
+  T_out += 16 * (size_t)p0;
+  if (status) status += p0;
+  const IcpScratch scr = icp_scratch(ws, R.icp, H, p0);
+  const SliceBufs b = slice_bufs(ws, R, H, W, levels, p0);
   const bool gate = p->max_corr_dist > 0.f;
-  const float* const* planes = b.planes;
-  const float* const* srcl = b.srcl;
-  const float* const* dstl = b.dstl;
-  for (int k = 0; k < levels; ++k) {
+  for (int k = k_first; k < levels; ++k) {
     const int l = levels - 1 - k;
-    const float* s_l = (l == 0) ? src_range : srcl[l];
-    const float* d_l = gate ? ((l == 0) ? dst_range : dstl[l]) : nullptr;
-    if (iters[k] > 0 && icp_iters_fits(H >> l, W >> l)) {
-      int rc = icp_iters_launch(src, dst, l, n, s_l, planes[l], d_l, T_out, p, status, scr, iters[k], st);
+    const float* s_l = (l == 0) ? src_range : b.srcl[l];
+    const float* d_l = gate ? ((l == 0) ? dst_range : b.dstl[l]) : nullptr;
+    if (iters[k] > 0 && icp_sched_fused(H >> l, W >> l, n)) {
+      int rc = icp_iters_launch(src, dst, l, n, s_l, b.planes[l], d_l, T_out, p, status, scr, iters[k], st);
       if (rc) return rc;
       continue;
     }
     for (int it = 0; it < iters[k]; ++it) {
-      int rc = icp_launch(src, dst, l, n, s_l, planes[l], d_l, T_out, p, 1, nullptr, nullptr, status, scr, st);
+      int rc = icp_launch(src, dst, l, n, s_l, b.planes[l], d_l, T_out, p, 1, nullptr, nullptr, status, scr, st);
       if (rc) return rc;
     }
   }
   return RIMG_OK;
+}
+
+// Registration of the pairs [p0, p0 + n) of a batch on one stream; every
+// buffer is addressed through the per-pair offsets of that range.
+int register_slice(const rimg_sensor* src, const rimg_sensor* dst, int p0, int n, const float* src_range,
+                   const float* dst_range, const double* T_init, double* T_out, int levels, const int* iters,
+                   const rimg_params* p, int* status, char* ws, const RegWs& R, cudaStream_t st) {
+  int rc = slice_begin(src, dst, p0, n, src_range, dst_range, T_init, T_out, levels, p, status, ws, R, st);
+  if (rc) return rc;
+  return slice_levels(src, dst, p0, n, src_range, dst_range, T_out, levels, iters, p, status, ws, R, 0, st);
 }
 
 // Internal streams for concurrent sub-batches, created once per device.
@@ -375,6 +398,33 @@ struct SubStreams {
 // run concurrently on internal streams forked from (and joined back into)
 // `st`: one sub-batch's FP64 solves, launch gaps and small coarse-level
 // kernels overlap another's work.
+// Whether the target's level l projects with the branch-free form (exact
+// inverse table, no azimuth offsets, power-of-two width), which the queue
+// kernel is built for.
+bool fast_level(const rimg_sensor* dst, int l) {
+  const rimg_level& L = dst->level[l];
+  return L.bins_exact && !L.has_theta && L.W > 0 && (L.W & (L.W - 1)) == 0;
+}
+
+// The number of leading schedule levels (coarsest first) that can run in the
+// persistent queue kernel: levels whose pair fits one block, with the
+// branch-free projection, no distance gate, and the one-block schedule for
+// every sub-batch size in `slice_sizes` (see rimg_autotune).
+int queue_prefix_of(const rimg_sensor* src, const rimg_sensor* dst, int levels, const rimg_params* p,
+                    const std::vector<int>& slice_sizes) {
+  if (p->max_corr_dist > 0.f) return 0;
+  int k = 0;
+  for (; k < levels; ++k) {
+    const int l = levels - 1 - k;
+    const int Hl = src->H >> l, Wl = src->W >> l;
+    if (!queue_level_ok(Hl, Wl) || !fast_level(dst, l)) break;
+    bool fused = true;
+    for (int n : slice_sizes) fused = fused && icp_sched_fused(Hl, Wl, n);
+    if (!fused) break;
+  }
+  return k;
+}
+
 int register_device(const rimg_sensor* src, const rimg_sensor* dst, int n_pairs, const float* src_range,
                     const float* dst_range, const double* T_init, double* T_out, int levels,
                     const int* iters, const rimg_params* p, int* status, char* ws,
@@ -413,6 +463,8 @@ int register_device(const rimg_sensor* src, const rimg_sensor* dst, int n_pairs,
 struct GroupWs {
   std::vector<size_t> off;    // byte offset of each group's registration workspace
   std::vector<RegWs> reg;
+  size_t queue = 0;           // QueueGroup[n_groups] for the persistent small-level kernel
+  size_t queue_counters = 0;  // unsigned[4]: one item counter per kernel form (receiver offset x Kahan)
   size_t end = 0;
 };
 
@@ -425,8 +477,18 @@ GroupWs groups_ws(int n_groups, const rimg_group* g) {
     w.reg.push_back(reg_ws(g[i].src->H, g[i].src->W, g[i].n_pairs, g[i].levels, 0));
     o += w.reg.back().end;
   }
+  w.queue = align_up(o);
+  o = w.queue + sizeof(QueueGroup) * (size_t)std::max(n_groups, 1);
+  w.queue_counters = align_up(o);
+  o = w.queue_counters + 4 * sizeof(unsigned);
   w.end = align_up(o);
   return w;
+}
+
+// The queued prefix of a group (queue_prefix_of over its sub-batch sizes).
+int queue_prefix(const rimg_group& g, const std::vector<int>& slice_sizes) {
+  if (g.n_pairs == 0) return 0;
+  return queue_prefix_of(g.src, g.dst, g.levels, g.params, slice_sizes);
 }
 
 struct Slice {
@@ -1017,6 +1079,16 @@ int rimg_register_groups(int n_groups, const rimg_group* groups, void* workspace
     RIMG_CUDA(cudaEventCreateWithFlags(&g_grp.fork, cudaEventDisableTiming));
     g_grp.device = dev;
   }
+  // The leading small levels of eligible groups run in one persistent queue
+  // launch per kernel form; every other level runs per sub-batch.
+  std::vector<std::vector<int>> sizes(n_groups);
+  for (const Slice& sl : slices) sizes[sl.group].push_back(sl.n);
+  std::vector<int> prefix(n_groups, 0);
+  bool any_queue = false;
+  for (int i = 0; i < n_groups; ++i) {
+    prefix[i] = queue_prefix(groups[i], sizes[i]);
+    any_queue = any_queue || prefix[i] > 0;
+  }
   // Longest-processing-time-first assignment of slices to internal streams;
   // slices of one group never share a workspace range, so all may overlap.
   const int nstreams = std::min<int>(kGroupStreams, (int)slices.size());
@@ -1027,18 +1099,101 @@ int rimg_register_groups(int n_groups, const rimg_group* groups, void* workspace
     assign[best].push_back(k);
     load[best] += slices[k].work;
   }
+  // Phase 1: per sub-batch, either the whole registration or (groups with a
+  // queued prefix) the set-up and pyramids only.
   RIMG_CUDA(cudaEventRecord(g_grp.fork, st));
   for (int i = 0; i < nstreams; ++i) {
     RIMG_CUDA(cudaStreamWaitEvent(g_grp.s[i], g_grp.fork, 0));
     for (int k : assign[i]) {
       const Slice& sl = slices[k];
       const rimg_group& g = groups[sl.group];
-      rc = register_slice(g.src, g.dst, sl.p0, sl.n, g.src_range, g.dst_range, g.T_init, g.T_out, g.levels,
-                          g.iters, g.params, g.status, ws + w.off[sl.group], w.reg[sl.group], g_grp.s[i]);
+      char* gws = ws + w.off[sl.group];
+      rc = prefix[sl.group] > 0
+               ? slice_begin(g.src, g.dst, sl.p0, sl.n, g.src_range, g.dst_range, g.T_init, g.T_out, g.levels,
+                             g.params, g.status, gws, w.reg[sl.group], g_grp.s[i])
+               : register_slice(g.src, g.dst, sl.p0, sl.n, g.src_range, g.dst_range, g.T_init, g.T_out, g.levels,
+                                g.iters, g.params, g.status, gws, w.reg[sl.group], g_grp.s[i]);
       if (rc) return rc;
     }
     RIMG_CUDA(cudaEventRecord(g_grp.join[i], g_grp.s[i]));
     RIMG_CUDA(cudaStreamWaitEvent(st, g_grp.join[i], 0));
+  }
+  if (!any_queue) return RIMG_OK;
+  // Phase 2: the queued small levels of every eligible pair, one persistent
+  // launch per kernel form (receiver offset, Kahan), most expensive groups
+  // first.
+  QueueGroup* dq = reinterpret_cast<QueueGroup*>(ws + w.queue);
+  unsigned* counters = reinterpret_cast<unsigned*>(ws + w.queue_counters);
+  int slot = 0;
+  for (int form = 0; form < 4; ++form) {
+    const bool r0 = (form & 1) != 0, kahan = (form & 2) != 0;
+    std::vector<std::pair<double, int>> order;
+    for (int i = 0; i < n_groups; ++i) {
+      const rimg_group& g = groups[i];
+      if (prefix[i] == 0) continue;
+      const bool g_r0 = g.src->r0 != 0.f || g.dst->r0 != 0.f;
+      if (g_r0 != r0 || (g.params->kahan != 0) != kahan) continue;
+      double cost = 0.0;
+      for (int k = 0; k < prefix[i]; ++k) {
+        const int l = g.levels - 1 - k;
+        cost += (double)(g.src->H >> l) * (g.src->W >> l) * g.iters[k];
+      }
+      order.push_back(std::make_pair(-cost, i));
+    }
+    if (order.empty()) continue;
+    std::sort(order.begin(), order.end());
+    std::vector<QueueGroup> hq(order.size());
+    int item0 = 0;
+    for (size_t q = 0; q < order.size(); ++q) {
+      const int i = order[q].second;
+      const rimg_group& g = groups[i];
+      char* gws = ws + w.off[i];
+      const RegWs& Rg = w.reg[i];
+      const SliceBufs b = slice_bufs(gws, Rg, g.src->H, g.src->W, g.levels, 0);
+      QueueGroup& Q = hq[q];
+      Q = QueueGroup{};
+      Q.n_lvl = prefix[i];
+      for (int k = 0; k < prefix[i]; ++k) {
+        const int l = g.levels - 1 - k;
+        Q.lvl[k].src = dev_level(g.src, l);
+        Q.lvl[k].dst = dev_level(g.dst, l);
+        Q.lvl[k].src_range = (l == 0) ? g.src_range : b.srcl[l];
+        Q.lvl[k].planes = reinterpret_cast<const float4*>(b.planes[l]);
+        Q.lvl[k].iters = g.iters[k];
+      }
+      Q.n_pairs = g.n_pairs;
+      Q.item0 = item0;
+      item0 += g.n_pairs;
+      Q.proj_iters = g.params->proj_iters;
+      Q.huber_delta = g.params->huber_delta;
+      Q.pose = g.T_out;
+      Q.sums = icp_scratch(gws, Rg.icp, g.src->H, 0).sums;
+      Q.status = g.status;
+    }
+    prof_before(st, K_ICP_QUEUE, -1, item0);
+    cudaError_t e = launch_icp_queue(hq.data(), (int)hq.size(), dq + slot, counters + form, r0, kahan, st);
+    prof_after(st);
+    if (e != cudaSuccess) return cuda_fail(e, "queue kernel");
+    slot += (int)hq.size();
+  }
+  // Phase 3: the remaining levels of the queued groups, per sub-batch.
+  RIMG_CUDA(cudaEventRecord(g_grp.fork, st));
+  for (int i = 0; i < nstreams; ++i) {
+    bool used = false;
+    for (int k : assign[i]) {
+      const Slice& sl = slices[k];
+      if (prefix[sl.group] == 0 || prefix[sl.group] >= groups[sl.group].levels) continue;
+      if (!used) RIMG_CUDA(cudaStreamWaitEvent(g_grp.s[i], g_grp.fork, 0));
+      used = true;
+      const rimg_group& g = groups[sl.group];
+      rc = slice_levels(g.src, g.dst, sl.p0, sl.n, g.src_range, g.dst_range, g.T_out, g.levels, g.iters, g.params,
+                        g.status, ws + w.off[sl.group], w.reg[sl.group], prefix[sl.group], g_grp.s[i]);
+      if (rc) return rc;
+    }
+    if (used) {
+      RIMG_CUDA(cudaEventRecord(g_grp.join[i], g_grp.s[i]));
+      RIMG_CUDA(cudaStreamWaitEvent(st, g_grp.join[i], 0));
+    }
   }
   return RIMG_OK;
 }
@@ -1058,6 +1213,7 @@ int rimg_autotune(int n_groups, const rimg_group* groups, void* workspace, size_
   RIMG_CUDA(cudaEventCreate(&e1));
   int entries = 0;
   std::vector<std::tuple<int, int, int>> done;
+  std::vector<std::tuple<int, int, int>> fitting;   // (H_l, W_l, pairs) of levels that fit one block
   for (const Slice& sl : slices) {
     const rimg_group& g = groups[sl.group];
     const int H = g.src->H, W = g.src->W;
@@ -1076,8 +1232,13 @@ int rimg_autotune(int n_groups, const rimg_group* groups, void* workspace, size_
                               cudaMemcpyDeviceToDevice, st));
     const IcpScratch scr = icp_scratch(gws, R.icp, H, sl.p0);
     RIMG_CUDA(cudaMemsetAsync(scr.counters, 0, sizeof(unsigned) * sl.n, st));
+    const double* init0 = g.T_init + 16 * (size_t)sl.p0;
+    auto restore_pose = [&]() {
+      return cudaMemcpyAsync(pose, init0, sizeof(double) * 16 * sl.n, cudaMemcpyDeviceToDevice, st);
+    };
     for (int l = 0; l < g.levels; ++l) {
       const int Hl = H >> l, Wl = W >> l;
+      const int k = g.levels - 1 - l;     // schedule index of level l
       const float* sl_src = (l == 0) ? s0 : b.srcl[l];
       const float* sl_dst = g.params->max_corr_dist > 0.f ? ((l == 0) ? g.dst_range + sl.p0 * N : b.dstl[l])
                                                            : nullptr;
@@ -1086,23 +1247,83 @@ int rimg_autotune(int n_groups, const rimg_group* groups, void* workspace, size_
       for (int T : {128, 256}) {
         for (int bp = 1; bp <= Hl; bp *= 2) {
           if ((long long)Hl * (Wl / 4) < (long long)T / 4 * bp) continue;   // blocks with no work
-          for (int rep = 0; rep < 4; ++rep) {
-            if (rep == 1) RIMG_CUDA(cudaEventRecord(e0, st));
-            rc = icp_launch(g.src, g.dst, l, sl.n, sl_src, b.planes[l], sl_dst, pose, g.params, 0, nullptr,
-                            nullptr, nullptr, scr, st, T, bp);
-            if (rc) return rc;
+          // the shortest of three runs of eight back-to-back launches (after one warm-up launch)
+          float ms = 1e30f;
+          rc = icp_launch(g.src, g.dst, l, sl.n, sl_src, b.planes[l], sl_dst, pose, g.params, 0, nullptr, nullptr,
+                          nullptr, scr, st, T, bp);
+          if (rc) return rc;
+          for (int run = 0; run < 3; ++run) {
+            RIMG_CUDA(cudaEventRecord(e0, st));
+            for (int rep = 0; rep < 8; ++rep) {
+              rc = icp_launch(g.src, g.dst, l, sl.n, sl_src, b.planes[l], sl_dst, pose, g.params, 0, nullptr,
+                              nullptr, nullptr, scr, st, T, bp);
+              if (rc) return rc;
+            }
+            RIMG_CUDA(cudaEventRecord(e1, st));
+            RIMG_CUDA(cudaEventSynchronize(e1));
+            float t = 0.f;
+            RIMG_CUDA(cudaEventElapsedTime(&t, e0, e1));
+            ms = std::min(ms, t);
           }
-          RIMG_CUDA(cudaEventRecord(e1, st));
-          RIMG_CUDA(cudaEventSynchronize(e1));
-          float ms = 0.f;
-          RIMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
           if (ms < best) { best = ms; best_t = T; best_b = bp; }
         }
       }
       icp_tune_set(Hl, Wl, sl.n, best_t, best_b);
       ++entries;
+      if (icp_iters_fits(Hl, Wl) && g.iters[k] > 0) {
+        const auto key = std::make_tuple(Hl, Wl, sl.n);
+        if (std::find(fitting.begin(), fitting.end(), key) == fitting.end()) fitting.push_back(key);
+      }
+    }
+    RIMG_CUDA(restore_pose());
+  }
+  // Per-level schedules, measured in context: for every level that fits one
+  // block (in every sub-batch size), the whole rimg_register_groups call is
+  // timed with that level run both ways -- all iterations in one block per
+  // pair (the persistent queue / one launch per level) and one association
+  // launch plus one FP64 solve launch per iteration -- and the faster kept.
+  // Timing the whole call keeps the concurrency of the other groups and
+  // sub-batches, which a level timed alone would not show.
+  auto time_call = [&](float* ms) -> int {   // the shortest of three runs of three calls
+    int r = rimg_register_groups(n_groups, groups, workspace, workspace_bytes, stream);
+    if (r) return r;
+    *ms = 1e30f;
+    for (int run = 0; run < 3; ++run) {
+      RIMG_CUDA(cudaEventRecord(e0, st));
+      for (int rep = 0; rep < 3; ++rep) {
+        r = rimg_register_groups(n_groups, groups, workspace, workspace_bytes, stream);
+        if (r) return r;
+      }
+      RIMG_CUDA(cudaEventRecord(e1, st));
+      RIMG_CUDA(cudaEventSynchronize(e1));
+      float t = 0.f;
+      RIMG_CUDA(cudaEventElapsedTime(&t, e0, e1));
+      *ms = std::min(*ms, t);
+    }
+    return RIMG_OK;
+  };
+  for (const auto& key : fitting) {
+    const int Hl = std::get<0>(key), Wl = std::get<1>(key), n = std::get<2>(key);
+    float t_fused = 0.f, t_multi = 0.f;
+    icp_sched_set(Hl, Wl, n, true);
+    if ((rc = time_call(&t_fused))) return rc;
+    icp_sched_set(Hl, Wl, n, false);
+    if ((rc = time_call(&t_multi))) return rc;
+    const bool fused = t_fused <= t_multi;
+    icp_sched_set(Hl, Wl, n, fused);
+    ++entries;
+    // launch shapes stay only for levels that run as per-iteration launches
+    if (fused) {
+      icp_tune_erase(Hl, Wl, n);
+      --entries;
     }
   }
+  // T_out ends as a copy of T_init
+  for (int i = 0; i < n_groups; ++i)
+    if (groups[i].n_pairs > 0 && groups[i].T_out != groups[i].T_init)
+      RIMG_CUDA(cudaMemcpyAsync(groups[i].T_out, groups[i].T_init, sizeof(double) * 16 * groups[i].n_pairs,
+                                cudaMemcpyDeviceToDevice, st));
+  RIMG_CUDA(cudaStreamSynchronize(st));
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return entries;

@@ -23,7 +23,7 @@ struct DevLevel {
 
 DevLevel dev_level(const rimg_sensor* s, int level);
 
-enum KernelId { K_UNPROJECT = 0, K_PYRAMID = 1, K_NORMALS = 2, K_ICP = 3, K_SRC_PYRAMID = 4, K_SOLVE = 5, K_SDF = 6, K_POINTS = 7, K_ICP_ITERS = 8 };
+enum KernelId { K_UNPROJECT = 0, K_PYRAMID = 1, K_NORMALS = 2, K_ICP = 3, K_SRC_PYRAMID = 4, K_SOLVE = 5, K_SDF = 6, K_POINTS = 7, K_ICP_ITERS = 8, K_ICP_QUEUE = 9 };
 
 // Launch-timing hooks (no-ops unless rimg_profile_begin was called).
 void prof_before(cudaStream_t st, int kernel, int level, int n);
@@ -60,6 +60,11 @@ struct IcpLaunch {
 void icp_grid(int H, int W, int n_pairs, int* bpp, int* rows_per_block, int* threads);
 void icp_tune_set(int H, int W, int n_pairs, int threads, int bpp);
 void icp_tune_clear();
+void icp_tune_erase(int H, int W, int n_pairs);
+// The schedule of a level that fits one block (rimg_autotune's choice for
+// (H, W, pairs); default: fused, all iterations in one block per pair).
+void icp_sched_set(int H, int W, int n_pairs, bool fused);
+bool icp_sched_fused(int H, int W, int n_pairs);
 int icp_tune_size();
 cudaError_t launch_icp(const IcpLaunch& a, cudaStream_t st);
 cudaError_t launch_solve(int n_pairs, double* sums, double* pose, int* status, cudaStream_t st);
@@ -72,6 +77,37 @@ cudaError_t launch_icp_iters(IcpLaunch a, int iters, cudaStream_t st);
 
 cudaError_t launch_center(const DevLevel& S, const DevLevel& D, int n_pairs, const float* src, const float* dst,
                           double* T_out, int* status, cudaStream_t st);
+
+// Persistent work queue over the small levels of uneven batches: every pair
+// of every listed group is one item, processed by one block -- all the
+// group's leading small levels (the coarsest, each fitting one block),
+// coarse to fine, every iteration with its FP64 update.  Items are taken
+// from an atomic counter; a block never waits for another.
+struct QueueLevel {
+  DevLevel src, dst;
+  const float* src_range;     // level-l source ranges [n][H_l][W_l]
+  const float4* planes;       // level-l target planes [n][H_l][W_l]
+  int iters;
+};
+struct QueueGroup {
+  QueueLevel lvl[RIMG_MAX_LEVELS];   // the leading small levels, coarse to fine
+  int n_lvl;
+  int n_pairs;
+  int item0;                          // the group's pairs are items item0 .. item0 + n_pairs - 1
+  int proj_iters;
+  float huber_delta;
+  double* pose;                       // [n][16], updated in place
+  double* sums;                       // [n][32], the last step's sums and step record
+  int* status;                        // [n] or null
+};
+constexpr int kQueueThreads = 256;
+// Whether level (H, W) runs in the queue kernel: it fits one block and its
+// chunks per row divide the block (row-stride cursors).
+bool queue_level_ok(int H, int W);
+// Writes the descriptors (device, `n_groups` entries) and launches the
+// persistent kernel on `st`; counter: device, zeroed here first.
+cudaError_t launch_icp_queue(const QueueGroup* host_groups, int n_groups, QueueGroup* dev_groups, unsigned* counter,
+                             bool r0, bool kahan, cudaStream_t st);
 
 cudaError_t launch_sdf(const DevLevel& L, int n_scans, const float* ranges, const double* poses, int nx, int ny,
                        int nz, float ox, float oy, float oz, float voxel, float trunc, int proj_iters, float* sdf,

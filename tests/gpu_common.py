@@ -60,18 +60,41 @@ def oracle_register(pair_src, pair_dst, sensor, T_init, levels, iters, params):
 # Shadowed per-level pose parity (the oracle side is oracle/shadow.py)
 
 POSE_TOL = 1e-4        # rad and m: per-level final poses against the oracle
-STEP_TOL = 1e-5        # rad and m: one Gauss-Newton step from the same pose and associations
+STEP_TOL = 1e-6        # rad and m: one Gauss-Newton step from the same pose and associations
 
 
-def gpu_truncated(R, torch, sens, src_t, dst_t, T0_t, levels, iters, params, k, j, ws):
-    """Poses [n, 4, 4] of the batch after the first k levels of the schedule
-    and j steps of level k (the same launches as the full registration, cut
-    short: every earlier step is computed identically)."""
-    it = [iters[q] for q in range(k)] + [j] + [0] * (levels - k - 1)
-    T1 = torch.empty_like(T0_t)
-    R.rimg_register(sens, sens, src_t.shape[0], src_t, dst_t, T0_t, T1, levels, it, params, None, ws)
-    torch.cuda.synchronize()
-    return T1.cpu().numpy().reshape(-1, 4, 4)
+def truncated_schedule(iters, k, j):
+    """The schedule cut after the first k levels and j steps of level k."""
+    return [iters[q] for q in range(k)] + [j] + [0] * (len(iters) - k - 1)
+
+
+def register_runner(R, torch, sens, src_t, dst_t, T0_t, levels, params):
+    """A function schedule -> poses [n, 4, 4] of the batch registered by
+    rimg_register with that schedule (the same launches as the full
+    registration, cut short: every earlier step is computed identically)."""
+    ws = torch.empty(R.rimg_register_workspace_bytes(sens, sens, src_t.shape[0], levels), dtype=torch.uint8,
+                     device="cuda")
+
+    def run(sched):
+        T1 = torch.empty_like(T0_t)
+        R.rimg_register(sens, sens, src_t.shape[0], src_t, dst_t, T0_t, T1, levels, list(sched), params, None, ws)
+        torch.cuda.synchronize()
+        return T1.cpu().numpy().reshape(-1, 4, 4)
+    return run
+
+
+def groups_runner(R, torch, group):
+    """A function schedule -> poses [n, 4, 4] of one rimg_register_groups
+    group registered alone with that schedule (a group's sub-batches and its
+    queue items do not depend on the other groups of a call)."""
+    def run(sched):
+        g = dict(group, iters=list(sched), T_out=torch.empty_like(group["T_init"]), status=None)
+        G = R.Groups([g])
+        ws = torch.empty(R.rimg_register_groups_workspace_bytes(G), dtype=torch.uint8, device="cuda")
+        R.rimg_register_groups(G, ws)
+        torch.cuda.synchronize()
+        return g["T_out"].cpu().numpy().reshape(-1, 4, 4)
+    return run
 
 
 def gpu_assoc(R, torch, sens, src, dst, level, T, params):
@@ -127,7 +150,7 @@ def oracle_pool_map(fn, tasks, procs=None):
 
 
 def shadowed_check(R, torch, sens, sensor, src, dst, levels, iters, params, o_params, pairs=None, final=None,
-                   T_init=None, pose_tol=POSE_TOL, step_tol=STEP_TOL, strict=True):
+                   T_init=None, pose_tol=POSE_TOL, step_tol=STEP_TOL, strict=True, runner=None):
     """Per-level parity of the batch registration of (src, dst) [n, H, W]
     against the oracle, on the pairs `pairs` (default all).
 
@@ -143,18 +166,21 @@ def shadowed_check(R, torch, sens, sensor, src, dst, levels, iters, params, o_pa
     near-tie, like every other pixel that differs at that step (where the
     trajectories split).  `final` (optional,
     [m, 4, 4] for the checked pairs) is the registration under test, which the
-    truncated runs must reproduce bit for bit.  Returns a report dict; with
+    truncated runs must reproduce bit for bit.  runner (optional): the
+    function schedule -> GPU poses of the registration under test (default:
+    rimg_register of the whole batch, see register_runner).  Returns a report
+    dict; with
     strict (the tests) a level that is beyond pose_tol and not explained
     fails an assertion, otherwise it is only counted (the benchmark)."""
     n = src.shape[0]
     pairs = list(range(n)) if pairs is None else list(pairs)
     T_init = np.tile(np.eye(4), (n, 1, 1)) if T_init is None else np.asarray(T_init)
-    src_t = torch.from_numpy(np.ascontiguousarray(src)).cuda()
-    dst_t = torch.from_numpy(np.ascontiguousarray(dst)).cuda()
-    T0_t = torch.from_numpy(np.ascontiguousarray(T_init.reshape(n, 16))).cuda()
-    ws = torch.empty(R.rimg_register_workspace_bytes(sens, sens, n, levels), dtype=torch.uint8, device="cuda")
-    ends = [gpu_truncated(R, torch, sens, src_t, dst_t, T0_t, levels, iters, params, k, iters[k], ws)
-            for k in range(levels)]
+    if runner is None:
+        src_t = torch.from_numpy(np.ascontiguousarray(src)).cuda()
+        dst_t = torch.from_numpy(np.ascontiguousarray(dst)).cuda()
+        T0_t = torch.from_numpy(np.ascontiguousarray(T_init.reshape(n, 16))).cuda()
+        runner = register_runner(R, torch, sens, src_t, dst_t, T0_t, levels, params)
+    ends = [runner(truncated_schedule(iters, k, iters[k])) for k in range(levels)]
     if final is not None:
         assert np.array_equal(ends[-1][pairs], np.asarray(final).reshape(-1, 4, 4)), "truncated runs differ"
     so = (sensor.phi_lut, sensor.theta_lut, sensor.r0)
@@ -167,8 +193,7 @@ def shadowed_check(R, torch, sens, sensor, src, dst, levels, iters, params, o_pa
         return report
     trajs = {}
     for k in sorted({k for _, k in bad}):
-        trajs[k] = [gpu_truncated(R, torch, sens, src_t, dst_t, T0_t, levels, iters, params, k, j, ws)
-                    for j in range(iters[k] + 1)]
+        trajs[k] = [runner(truncated_schedule(iters, k, j)) for j in range(iters[k] + 1)]
     tasks = []
     for i, k in bad:
         l = levels - 1 - k

@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 from synth import CONFIGS, make_pairs
-from tests.gpu_common import gpu_sensor, oracle_params, shadowed_check
+from tests.gpu_common import gpu_sensor, oracle_params, shadowed_check, groups_runner
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -74,5 +74,5 @@ def test_register_groups_graph_replay(R):
     # the replayed poses against the oracle, level by level, one pair per size
     for g, (cfg, s, src, dst) in zip(groups, keep):
         rep = shadowed_check(R, torch, g["src"], s, src, dst, cfg.levels, cfg.iters, g["params"], oracle_params(cfg),
-                             pairs=[0], final=g["T_out"][:1].cpu().numpy())
+                             pairs=[0], final=g["T_out"][:1].cpu().numpy(), runner=groups_runner(R, torch, g))
         print(cfg.name, rep)

@@ -8,7 +8,7 @@ is accepted only when the test itself shows why, step by step (see
 tests/gpu_common.shadowed_check and oracle/shadow.py): every GPU association
 equals the oracle's at the same pose except on near-tie pixels, every GPU
 step equals the oracle's step from the same pose and associations within
-1e-5, and the level contains a near-tie decided the other way.  The counts
+1e-6, and the level contains a near-tie decided the other way.  The counts
 are printed."""
 import json
 

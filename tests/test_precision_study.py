@@ -8,7 +8,7 @@ shadowed check of tests/gpu_common.py): the oracle runs each level of the
 GPU's level-end pose must be within 1e-4 rad / 1e-4 m of the oracle's.  A
 level beyond that is accepted only with the step-by-step reading (GPU
 associations equal to the oracle's off near-ties, each GPU step equal to the
-oracle's from the same pose and associations within 1e-5, a near-tie decided
+oracle's from the same pose and associations within 1e-6, a near-tie decided
 the other way).  The whole registrations' errors against the oracle's whole
 registrations are reported pair by pair.
 
