@@ -242,6 +242,43 @@ def test_configs_cover_both_projection_forms(R):
     assert all(_fast_projection(gpu_sensor(R, s, 4), l) for l in range(4))   # the headline sensor
 
 
+@pytest.mark.parametrize("name,r0", [("pair64x1024", 0.0), ("pair32x512", 0.015)])
+def test_fast_form_equals_general_form(R, name, r0):
+    """The branch-free projection (exact table, one comparison, column wrapped
+    by a mask) takes the same decisions as the general form with the boundary
+    walk and the conditional wraps: a step's 29 sums are bit-identical between
+    the two (the association output selects the general form; both walk chunks
+    in the same order), at every level, at poses that move points across the
+    field-of-view edges."""
+    import dataclasses
+    cfg = dataclasses.replace(CONFIGS[name], config_id=91 if r0 else CONFIGS[name].config_id, r0=r0)
+    levels = cfg.levels
+    pair = make_pair(cfg, 1)
+    s = pair["sensor"]
+    sens = gpu_sensor(R, s, levels)
+    assert all(_fast_projection(sens, l) for l in range(levels))
+    params = R.rimg_default_params(huber_delta=cfg.huber_delta)
+    src = torch.from_numpy(pair["src_range"])[None].cuda()
+    dst = torch.from_numpy(pair["dst_range"])[None].cuda()
+    planes, _ = planes_for(R, torch, sens, dst, params)
+    spyr = src_pyramid(R, torch, sens, src)
+    ws = torch.empty(R.rimg_icp_workspace_bytes(sens, 1), dtype=torch.uint8, device="cuda")
+    for pose in (np.eye(4), O.se3_exp(np.array([0.05, -0.08, 0.02, 0.3, -0.2, 0.9])) @ pair["T_gt"],
+                 O.se3_exp(np.array([0.0, 0.2, 0.0, 0.0, 0.0, -1.5]))):
+        for level in range(levels):
+            out = []
+            for with_assoc in (True, False):
+                T = torch.from_numpy(pose.reshape(1, 16).copy()).cuda()
+                o29 = torch.zeros((1, 29), dtype=torch.float64, device="cuda")
+                assoc = (torch.empty((1, s.H >> level, s.W >> level), dtype=torch.int32, device="cuda")
+                         if with_assoc else None)
+                R.rimg_icp_step(sens, sens, level, 1, spyr[level], planes[level], None, T, params, 0, o29, assoc,
+                                None, ws)
+                torch.cuda.synchronize()
+                out.append(o29.cpu().numpy())
+            assert np.array_equal(out[0], out[1]), (level, out[0] - out[1])
+
+
 @pytest.mark.parametrize("pose_kind", ["identity", "near"])
 def test_icp_step_parity_fast_projection_with_receiver_offset(R, pose_kind):
     """Exact tables and no azimuth offsets, with a receiver offset r0 = 1.5 cm:
