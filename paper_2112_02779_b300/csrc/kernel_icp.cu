@@ -324,9 +324,33 @@ __device__ __forceinline__ float warp_scatter_sum(const float2 (&t)[kPairs], int
 // divide THREADS), so a cursor advances by rows only.  FAST: the target
 // level's inverse table is exact, it has no azimuth offsets and its width is
 // a power of two (the projection has no branch).
+// The first two source-range fetches of icp_block_terms (chunks tid and
+// tid + THREADS of rows [v_begin, v_end)), issued and committed as one
+// cp.async group by a caller that has other latency to overlap them with
+// (the pose load at the start of a block); icp_block_terms is then called
+// with prefetched = true.
+template <int THREADS>
+__device__ __forceinline__ void icp_prefetch(const IcpLaunch& a, IcpSmem<THREADS>& sm, int pair, int v_begin,
+                                             int v_end) {
+  const int tid = threadIdx.x;
+  const int W = a.src.W;
+  const int cpr = W >> 2;
+  const int nchunks = max(0, v_end - v_begin) * cpr;
+  const float* src = a.src_range + pair * (long long)a.src.H * W;
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const int c = tid + j * THREADS;
+    if (c < nchunks) {
+      const int v = v_begin + c / cpr, cu = c - (c / cpr) * cpr;
+      cp_async16_zfill(&sm.src[j][tid], src + (long long)v * W + (cu << 2), true);
+    }
+  }
+  cp_async_commit();
+}
+
 template <bool R0, bool GATE, bool ASSOC, bool KAHAN, int THREADS, bool ROWSTRIDE = false, bool FAST = false>
 __device__ __forceinline__ void icp_block_terms(const IcpLaunch& a, IcpSmem<THREADS>& sm, int pair, int v_begin,
-                                                int v_end) {
+                                                int v_end, bool prefetched = false) {
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
   const DevLevel& S = a.src;
@@ -485,9 +509,14 @@ __device__ __forceinline__ void icp_block_terms(const IcpLaunch& a, IcpSmem<THRE
   // Unrolled by two so slots are constants.
   static_assert(kRing == 2, "the pipeline below is written for a two-slot ring");
   Pts P0, P1;
-  if (nmine > 0) fetch_src(0);
-  if (nmine > 1) fetch_src(1);
-  cp_async_commit();
+  if (prefetched) {          // chunks 0 and 1 were fetched by icp_prefetch
+    if (nmine > 0) advance(cf);
+    if (nmine > 1) advance(cf);
+  } else {
+    if (nmine > 0) fetch_src(0);
+    if (nmine > 1) fetch_src(1);
+    cp_async_commit();
+  }
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   int i = 0;
   while (true) {
@@ -542,11 +571,13 @@ __global__ void __launch_bounds__(THREADS, RIMG_ICP_THREADS_PER_SM / THREADS) k_
   const int tid = threadIdx.x;
   const int pair = blockIdx.x / a.bpp;
   const int blk = blockIdx.x - pair * a.bpp;
+  const int v_begin = blk * a.rows_per_block;
+  const int v_end = min(a.src.H, v_begin + a.rows_per_block);
+  // the first source ranges are fetched while the pose is loaded
+  icp_prefetch<THREADS>(a, sm, pair, v_begin, v_end);
   if (tid < 12) reinterpret_cast<float*>(sm.T4)[tid] = (float)a.pose[pair * 16 + tid];
   __syncthreads();
-  const int v_begin = blk * a.rows_per_block;
-  icp_block_terms<R0, GATE, ASSOC, KAHAN, THREADS, ROWSTRIDE, FAST>(a, sm, pair, v_begin,
-                                                                    min(a.src.H, v_begin + a.rows_per_block));
+  icp_block_terms<R0, GATE, ASSOC, KAHAN, THREADS, ROWSTRIDE, FAST>(a, sm, pair, v_begin, v_end, true);
   if (a.bpp == 1) {
     // one block per pair: the block total is the pair total
     if (tid < kRed) {
