@@ -16,6 +16,14 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "librimg.so")
 SOURCES = ["rimg_api.cu", "kernels_prep.cu", "kernel_icp.cu", "rimg_noalloc.cu", "kernel_gemm.cu", "rimg_cnn.cu", "kernel_sdf.cu", "kernel_points.cu", "kernel_center.cu"]
+# Per-file nvcc options of the default build.  The FP32 registration, sensor
+# and fusion kernels flush denormals (FP32 values below 2^-126 are zero in
+# their inputs and results): ranges, coordinates and normals are never that
+# small, and it removes the denormal handling around reciprocal and
+# reciprocal-square-root approximations in the per-pixel code.
+_FTZ = ["-ftz=true"]
+SOURCE_FLAGS = {"kernel_icp.cu": _FTZ, "kernels_prep.cu": _FTZ, "kernel_sdf.cu": _FTZ, "kernel_points.cu": _FTZ,
+                "kernel_center.cu": _FTZ}
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -33,11 +41,13 @@ def up_to_date():
     return all(os.path.getmtime(f) <= t for f in _inputs())
 
 
-def build(verbose=False, force=False, out=None, defines=()):
+def build(verbose=False, force=False, out=None, defines=(), flags=None):
     """Compile every CUDA source into one shared library (default: the
-    in-tree librimg.so).  `defines` are extra -D tunables (e.g. RIMG_RING=2).
-    Sources compile to objects in parallel, then one link step."""
+    in-tree librimg.so).  `defines` are extra -D tunables (e.g. RIMG_RING=2);
+    `flags` maps a source file to extra nvcc options for it alone.  Sources
+    compile to objects in parallel, then one link step."""
     lib = out or LIB
+    flags = dict(SOURCE_FLAGS if flags is None else flags)
     if not force and out is None and not defines and up_to_date():
         return LIB
     os.makedirs(os.path.dirname(lib), exist_ok=True)
@@ -50,7 +60,8 @@ def build(verbose=False, force=False, out=None, defines=()):
 
     def compile_one(src):
         obj = os.path.join(objdir, os.path.splitext(src)[0] + ".o")
-        res = subprocess.run(common + ["-c", "-o", obj, os.path.join(CSRC, src)], capture_output=True, text=True)
+        res = subprocess.run(common + list(flags.get(src, ())) + ["-c", "-o", obj, os.path.join(CSRC, src)],
+                             capture_output=True, text=True)
         return src, obj, res
 
     from concurrent.futures import ThreadPoolExecutor

@@ -281,7 +281,7 @@ struct IcpSmem {
 
 // Chunks summed plainly per thread between two compensated warp steps.
 #ifndef RIMG_WARP_FLUSH
-#define RIMG_WARP_FLUSH 8
+#define RIMG_WARP_FLUSH 16
 #endif
 constexpr int kWarpFlush = RIMG_WARP_FLUSH;
 static_assert(kWarpFlush >= 1, "at least one chunk between warp steps");
