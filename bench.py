@@ -292,17 +292,20 @@ def pose_check(levels_report, whole_err, bar=1e-4):
     oracle (levels_report: the shadowed check's report -- every level of the
     schedule run by the oracle from the pose the GPU started it from; a level
     beyond the bar is counted as explained when the step-by-step reading shows
-    near-tie decisions with every step's arithmetic matching), plus the whole
-    registrations' differences (whole_err [n, 2], context)."""
+    every step's arithmetic matching and the trajectories parted at a near-tie
+    decision ("near-tie") or, on an ill-conditioned level, by the FP32 sums
+    the level amplifies ("conditioning")), plus the whole registrations'
+    differences (whole_err [n, 2], context)."""
     whole = np.asarray(whole_err, np.float64).reshape(-1, 2)
     r = levels_report
     return {"pairs": int(r["pairs"]), "levels_checked": int(r["levels_checked"]),
             "levels_within_1e-4": int(r["levels_checked"] - len(r["beyond"])),
             "levels_beyond_1e-4_explained": int(r["explained"]),
             "levels_beyond_1e-4_unexplained": int(r["unexplained"]),
+            "explained_by_kind": dict(r.get("by_kind", {})),
             "max_level_err": [float(x) for x in r["max_err"]],
             "beyond": [{k: b[k] for k in ("pair", "level_index", "err", "split", "split_ties", "split_off_tie",
-                                          "step_err_given_max", "explained")}
+                                          "step_err_given_max", "explained")} | {"kind": b.get("kind")}
                        for b in r["beyond"]],
             "whole_registration_within_1e-4": int(np.sum(np.all(whole <= bar, axis=1))),
             "whole_registration_median_err": [float(np.median(whole[:, 0])), float(np.median(whole[:, 1]))]}

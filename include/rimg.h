@@ -382,6 +382,17 @@ int rimg_register_groups(int n_groups, const rimg_group* groups, void* workspace
  * negative status.  rimg_autotune_clear empties the table. */
 int rimg_autotune(int n_groups, const rimg_group* groups, void* workspace, size_t workspace_bytes, void* stream);
 int rimg_autotune_clear(void);
+/* One entry of the same table set by hand (a saved tuning, or a test that
+ * pins a candidate): for levels of H_l x W_l pixels registered in launches of
+ * n_pairs pairs, the association launch shape -- threads per block (128 or
+ * 256; 0 removes the shape entry) and blocks per pair (1 .. H_l, rounded as
+ * the tuner rounds: whole rows per block) -- and the schedule: 1 all
+ * iterations in one block per pair (taken only where the pair fits one
+ * block), 0 one association launch and one FP64 solve launch per iteration,
+ * -1 leaves the schedule entry as it is.  Returns RIMG_OK or
+ * RIMG_ERR_INVALID_ARG (non-positive sizes, other thread counts, blocks per
+ * pair outside 1 .. H_l, schedule outside -1 .. 1). */
+int rimg_autotune_set(int H_l, int W_l, int n_pairs, int threads, int blocks_per_pair, int schedule);
 
 /* ---------------------------------------------------------------------------
  * rimg_register with HOST inputs and outputs: copies src_range/dst_range

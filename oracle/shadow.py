@@ -37,14 +37,26 @@ import numpy as np
 from . import rimg_oracle as O
 
 
-def step_with_assoc(src_pts, src_valid, target, level, T, params, assoc):
+def step_with_assoc(src_pts, src_valid, target, level, T, params, assoc, return_terms=False):
     """The oracle's Gauss-Newton step from T with the association indices
-    `assoc` imposed (icp_terms' assoc argument): the step's arithmetic alone."""
+    `assoc` imposed (icp_terms' assoc argument): the step's arithmetic alone.
+    return_terms adds the step's association terms."""
     rng_l, n_l, nv_l, ph, th = target.level(level)
     terms = O.icp_terms(src_pts, src_valid, T, rng_l, n_l, nv_l, ph, th, target.r0,
                         params.get("huber_delta", 0.5), params.get("max_corr_dist", 0.0), assoc=assoc)
     T_new, _ = O.gn_update(T, terms)
-    return T_new
+    return (T_new, terms) if return_terms else T_new
+
+
+def system_condition(terms):
+    """2-norm condition number of the step's 6x6 Gauss-Newton matrix
+    J^T W J (the ratio of its extreme eigenvalues; inf when it is singular).
+    A relative perturbation eps of the matrix and of the right-hand side
+    moves the solution by up to about cond * eps * |x| (first-order
+    perturbation bound of a linear system), which is how far reduced sums
+    carried in a lower precision can move one step."""
+    ev = np.linalg.eigvalsh(np.asarray(terms["H"], np.float64))
+    return float(ev[-1] / ev[0]) if ev[0] > 0 else float("inf")
 
 
 def run_level(src_pts, src_valid, target, level, T0, steps, params, keep_terms=False):
@@ -99,6 +111,10 @@ def explain_level(src_range, dst_range, sensor, levels, k, iters, params, traj, 
       split_off_tie       of those, the ones the oracle flags as near-ties at neither pose
       drift[j]            (rad, m) between traj[j] and the oracle's own trajectory
                           from traj[0]
+      cond[j]             condition number of the step's 6x6 system with the
+                          registration's associations imposed (system_condition)
+      step_size[j]        size of that oracle step: its rotation angle (rad) and translation
+                          change (m) combined as sqrt(angle^2 + change^2), mixed as in the solve
     """
     sp, st, r0 = sensor
     l = levels - 1 - k
@@ -108,7 +124,7 @@ def explain_level(src_range, dst_range, sensor, levels, k, iters, params, traj, 
     n = iters[k]
     out = dict(step_err=np.zeros((n, 2)), step_err_given=np.zeros((n, 2)), mismatch=np.zeros(n, int),
                off_tie_mismatch=np.zeros(n, int), split=None, split_ties=0, split_off_tie=0,
-               drift=np.zeros((n + 1, 2)))
+               drift=np.zeros((n + 1, 2)), cond=np.zeros(n), step_size=np.zeros(n))
     T_own = np.array(traj[0], np.float64)
     for j in range(n):
         out["drift"][j] = O.pose_error(traj[j], T_own)
@@ -119,7 +135,10 @@ def explain_level(src_range, dst_range, sensor, levels, k, iters, params, traj, 
         diff_a = a != t["assoc"]
         out["mismatch"][j] = int(diff_a.sum())
         out["off_tie_mismatch"][j] = int((diff_a & ~t["near_tie"]).sum())
-        out["step_err_given"][j] = O.pose_error(traj[j + 1], step_with_assoc(P, sv, target, l, traj[j], params, a))
+        T_given, t_given = step_with_assoc(P, sv, target, l, traj[j], params, a, return_terms=True)
+        out["step_err_given"][j] = O.pose_error(traj[j + 1], T_given)
+        out["cond"][j] = system_condition(t_given)
+        out["step_size"][j] = float(np.hypot(*O.pose_error(T_given, traj[j])))
         diff_b = t["assoc"] != ot["assoc"]
         if out["split"] is None and (diff_a.any() or diff_b.any()):
             out["split"] = j

@@ -1334,6 +1334,18 @@ int rimg_autotune_clear(void) {
   return RIMG_OK;
 }
 
+int rimg_autotune_set(int H_l, int W_l, int n_pairs, int threads, int blocks_per_pair, int schedule) {
+  if (H_l <= 0 || W_l <= 0 || n_pairs <= 0 || schedule < -1 || schedule > 1) return RIMG_ERR_INVALID_ARG;
+  if (threads != 0 && threads != 128 && threads != 256) return RIMG_ERR_INVALID_ARG;
+  if (threads != 0 && (blocks_per_pair < 1 || blocks_per_pair > H_l)) return RIMG_ERR_INVALID_ARG;
+  if (threads == 0)
+    icp_tune_erase(H_l, W_l, n_pairs);
+  else
+    icp_tune_set(H_l, W_l, n_pairs, threads, blocks_per_pair);
+  if (schedule >= 0) icp_sched_set(H_l, W_l, n_pairs, schedule == 1);
+  return RIMG_OK;
+}
+
 int rimg_gemm_bf16(int M, int N, int K, const void* A, int lda, const void* B, int ldb, float* C, int ldc,
                    void* C_bf16, const float* bias, int relu, int splits, int* err, void* stream) {
   if (M < 0 || N < 0 || K < 0 || splits < 1) return RIMG_ERR_INVALID_ARG;

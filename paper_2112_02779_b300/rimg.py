@@ -64,6 +64,7 @@ _sig("rimg_register_groups_workspace_bytes", _c_int, _c_int, _P(rimg_group), _P(
 _sig("rimg_register_groups", _c_int, _c_int, _P(rimg_group), _vp, _c_size, _vp)
 _sig("rimg_autotune", _c_int, _c_int, _P(rimg_group), _vp, _c_size, _vp)
 _sig("rimg_autotune_clear", _c_int)
+_sig("rimg_autotune_set", _c_int, _c_int, _c_int, _c_int, _c_int, _c_int, _c_int)
 _sig("rimg_gemm_bf16", _c_int, _c_int, _c_int, _c_int, _vp, _c_int, _vp, _c_int, _vp, _c_int, _vp, _vp, _c_int,
      _c_int, _vp, _vp)
 _sig("rimg_cnn_param_count", _c_int, _P(_c_size))
@@ -319,6 +320,10 @@ def rimg_autotune(groups, workspace, stream=None):
 
 def rimg_autotune_clear():
     _check("rimg_autotune_clear", _lib.rimg_autotune_clear())
+
+
+def rimg_autotune_set(H_l, W_l, n_pairs, threads, blocks_per_pair, schedule=-1):
+    _check("rimg_autotune_set", _lib.rimg_autotune_set(H_l, W_l, n_pairs, threads, blocks_per_pair, schedule))
 
 
 def rimg_gemm_bf16(A, B, C, C_bf16=None, bias=None, relu=False, splits=1, err=None, stream=None):

@@ -20,8 +20,9 @@ def _bench():
 def test_pose_check_summarises_the_per_level_report():
     b = _bench()
     rep = {"pairs": 3, "levels_checked": 12, "max_err": [2e-4, 3e-4], "explained": 1, "unexplained": 1,
+           "by_kind": {"near-tie": 1},
            "beyond": [dict(pair=1, level_index=3, err=[2e-4, 3e-4], split=4, split_ties=2, split_off_tie=0,
-                           step_err_given_max=[1e-7, 2e-7], explained=True),
+                           step_err_given_max=[1e-7, 2e-7], explained=True, kind="near-tie"),
                       dict(pair=2, level_index=2, err=[1e-4, 1.5e-4], split=None, split_ties=0, split_off_tie=0,
                            step_err_given_max=[1e-3, 1e-3], explained=False)]}
     whole = [(1e-6, 2e-6), (2e-4, 3e-4), (5e-5, 1e-5)]
@@ -31,6 +32,7 @@ def test_pose_check_summarises_the_per_level_report():
     assert r["whole_registration_within_1e-4"] == 2
     assert r["whole_registration_median_err"] == [5e-5, 1e-5]
     assert [x["pair"] for x in r["beyond"]] == [1, 2]
+    assert r["explained_by_kind"] == {"near-tie": 1} and [x["kind"] for x in r["beyond"]] == ["near-tie", None]
 
 
 def test_committed_profiles_carry_the_keys_bench_reads():

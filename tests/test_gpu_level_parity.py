@@ -4,9 +4,11 @@ test: every level of every pair's schedule run by the oracle from the pose
 the GPU started it from, level-end poses within 1e-4 rad / 1e-4 m, or the
 level explained step by step (GPU associations equal to the oracle's off
 near-ties, each step's arithmetic within 1e-6 with the GPU's associations
-imposed, the split at a near-tie).
+imposed -- or within the FP32 perturbation bound of an ill-conditioned step
+-- and the split at a near-tie, or no split on an ill-conditioned level).
 
-Cases: the 32 x 512 workload (branch-free projection), the interlaced 64 x 512
+Cases: the 32 x 512 workload (branch-free projection; 8 pairs, and 40 pairs,
+one of which diverges), the interlaced 64 x 512
 sensor with azimuth offsets and a 1.5 cm receiver offset (general form with
 the receiver-offset fixed point), the 32 x 512 sensor with a receiver offset
 (branch-free form inside the fixed point), the distance gate, plain FP32
@@ -45,6 +47,9 @@ def _pairs(cfg, n):
 
 CASES = {
     "pair32x512": (lambda: CONFIGS["pair32x512"], 8, {}, {}),
+    # 40 pairs: pair 27 diverges (a few dozen associations, steps of metres,
+    # condition numbers 1e3-1e5), the level accepted by conditioning
+    "pair32x512_40": (lambda: CONFIGS["pair32x512"], 40, {}, {}),
     "lut64x512_offsets_r0": (lambda: CONFIGS["lut64x512"], 6, {}, {}),
     "pair32x512_r0_fast": (lambda: dataclasses.replace(CONFIGS["pair32x512"], name="pair32x512_r0", config_id=91,
                                                        r0=0.015), 6, {}, {}),
@@ -66,6 +71,6 @@ def test_per_level_parity(R, case):
         o_params["normal_method"] = o_kw["normal_method"]
     src, dst = _pairs(cfg, n)
     rep = shadowed_check(R, torch, sens, s, src, dst, cfg.levels, cfg.iters, params, o_params)
-    print(case, json.dumps({k: rep[k] for k in ("pairs", "levels_checked", "max_err", "explained")}))
+    print(case, json.dumps({k: rep[k] for k in ("pairs", "levels_checked", "max_err", "explained", "by_kind")}))
     assert rep["levels_checked"] == n * cfg.levels
     assert len(rep["beyond"]) <= max(1, int(0.1 * rep["levels_checked"]))
