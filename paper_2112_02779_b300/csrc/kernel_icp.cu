@@ -279,6 +279,44 @@ struct IcpSmem {
   int last;
 };
 
+// Per-row constants of the folded unprojection and transform (see issue in
+// icp_block_terms), one table per block after its IcpSmem: for row v_begin + i
+// of the block, entries 3i .. 3i + 2 hold A_v, B_v, C_v with the translation
+// t_x, t_y, t_z in .w.  Blocks cover at most kMaxBlockRows rows.
+constexpr int kMaxBlockRows = 1024;
+template <int THREADS>
+__host__ __device__ constexpr size_t row_table_offset() {
+  return (sizeof(IcpSmem<THREADS>) + 15) & ~size_t(15);
+}
+template <int THREADS>
+__host__ __device__ constexpr size_t icp_smem_bytes(int rows) {
+  return row_table_offset<THREADS>() + sizeof(float4) * 3 * (size_t)rows;
+}
+template <int THREADS>
+__device__ __forceinline__ float4* row_table(IcpSmem<THREADS>& sm) {
+  return reinterpret_cast<float4*>(reinterpret_cast<char*>(&sm) + row_table_offset<THREADS>());
+}
+
+// Fills the row table for rows [v_begin, v_begin + nrows) of level S at the
+// pose in sm.T4.  With the row's cos/sin of elevation and azimuth offset and
+// the rotation columns R0, R1, R2,
+//   R p = r (cos u A + sin u B + C),  A = cos(phi) (cos(th) R0 + sin(th) R1),
+//   B = cos(phi) (cos(th) R1 - sin(th) R0),  C = sin(phi) R2.
+// The caller synchronises the block before the table is read.
+template <int THREADS>
+__device__ __forceinline__ void icp_row_table(const DevLevel& S, IcpSmem<THREADS>& sm, int v_begin, int nrows) {
+  float4* rt = row_table(sm);
+  const float4 T0 = sm.T4[0], T1 = sm.T4[1], T2 = sm.T4[2];
+  for (int i = threadIdx.x; i < nrows; i += THREADS) {
+    const float4 rw = __ldg(S.rows + v_begin + i);
+    const float q0 = rw.x * rw.z, q1 = rw.x * rw.w;
+    rt[3 * i] = make_float4(fmaf(q0, T0.x, q1 * T0.y), fmaf(q0, T1.x, q1 * T1.y), fmaf(q0, T2.x, q1 * T2.y), T0.w);
+    rt[3 * i + 1] = make_float4(fmaf(q0, T0.y, -q1 * T0.x), fmaf(q0, T1.y, -q1 * T1.x), fmaf(q0, T2.y, -q1 * T2.x),
+                                T1.w);
+    rt[3 * i + 2] = make_float4(rw.y * T0.z, rw.y * T1.z, rw.y * T2.z, T2.w);
+  }
+}
+
 // Chunks summed plainly per thread between two compensated warp steps.
 #ifndef RIMG_WARP_FLUSH
 #define RIMG_WARP_FLUSH 16
@@ -318,8 +356,9 @@ __device__ __forceinline__ float warp_scatter_sum(const float2 (&t)[kPairs], int
 #define RIMG_ICP_THREADS_PER_SM 512
 #endif
 // One block's share of a step: the rows [v_begin, v_end) of pair `pair` at
-// the pose in sm.T4.  On return (after a block barrier) sm.red[w][l] holds
-// warp w's component l of the 29 sums (lane order, see kFlat).
+// the pose in sm.T4, whose row table (icp_row_table) the caller has filled.
+// On return (after a block barrier) sm.red[w][l] holds warp w's component l
+// of the 29 sums (lane order, see kFlat).
 // ROWSTRIDE: the thread stride is a whole number of rows (chunks per row
 // divide THREADS), so a cursor advances by rows only.  FAST: the target
 // level's inverse table is exact, it has no azimuth offsets and its width is
@@ -363,6 +402,7 @@ __device__ __forceinline__ void icp_block_terms(const IcpLaunch& a, IcpSmem<THRE
   const float* drange = GATE ? a.dst_range + pair * Nd : nullptr;
   const float inv_delta = a.huber_delta > 0.f ? 1.f / a.huber_delta : 0.f;
   const float gate2 = a.max_corr_dist * a.max_corr_dist;
+  const float4* rowtab = row_table(sm);
 
   float2 t[kPairs];
 #pragma unroll
@@ -412,20 +452,14 @@ __device__ __forceinline__ void icp_block_terms(const IcpLaunch& a, IcpSmem<THRE
     advance(ci);
     const float4 r4 = sm.src[slot][tid];
     const float rr[4] = {r4.x, r4.y, r4.z, r4.w};
-    const float4 rw = __ldg(S.rows + v);
     const float4 cc4 = __ldg(reinterpret_cast<const float4*>(S.cos_u + u0));
     const float4 ss4 = __ldg(reinterpret_cast<const float4*>(S.sin_u + u0));
     const float cs[4] = {cc4.x, cc4.y, cc4.z, cc4.w}, sn[4] = {ss4.x, ss4.y, ss4.z, ss4.w};
-    const float4 T0 = sm.T4[0], T1 = sm.T4[1], T2 = sm.T4[2];
-    // Unprojection and transform folded: with the row's cos/sin(phi) and
-    // cos/sin(theta_lut) and the rotation columns R0, R1, R2,
-    //   R p = r (cs A + sn B + C),  A = cos(phi) (cos(th) R0 + sin(th) R1),
-    //   B = cos(phi) (cos(th) R1 - sin(th) R0),  C = sin(phi) R2,
-    // plus r0 (cs R0 + sn R1) with a receiver offset.
-    const float q0 = rw.x * rw.z, q1 = rw.x * rw.w;
-    const float3 A = make_float3(fmaf(q0, T0.x, q1 * T0.y), fmaf(q0, T1.x, q1 * T1.y), fmaf(q0, T2.x, q1 * T2.y));
-    const float3 B = make_float3(fmaf(q0, T0.y, -q1 * T0.x), fmaf(q0, T1.y, -q1 * T1.x), fmaf(q0, T2.y, -q1 * T2.x));
-    const float3 C = make_float3(rw.y * T0.z, rw.y * T1.z, rw.y * T2.z);
+    // Unprojection and transform folded (icp_row_table): R p + t =
+    // r (cs A + sn B + C) + t, plus r0 (cs R0 + sn R1) with a receiver offset.
+    const float4* rt = rowtab + 3 * (v - v_begin);
+    const float4 A = rt[0], B = rt[1], C = rt[2];
+    const float4 T0 = sm.T4[0], T1 = sm.T4[1], T2 = sm.T4[2];   // read with a receiver offset only
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const bool valid = range_ok(rr[q]);
@@ -433,9 +467,9 @@ __device__ __forceinline__ void icp_block_terms(const IcpLaunch& a, IcpSmem<THRE
       const float Dx = fmaf(cs[q], A.x, fmaf(sn[q], B.x, C.x));
       const float Dy = fmaf(cs[q], A.y, fmaf(sn[q], B.y, C.y));
       const float Dz = fmaf(cs[q], A.z, fmaf(sn[q], B.z, C.z));
-      const float ox = R0 ? fmaf(S.r0 * cs[q], T0.x, fmaf(S.r0 * sn[q], T0.y, T0.w)) : T0.w;
-      const float oy = R0 ? fmaf(S.r0 * cs[q], T1.x, fmaf(S.r0 * sn[q], T1.y, T1.w)) : T1.w;
-      const float oz = R0 ? fmaf(S.r0 * cs[q], T2.x, fmaf(S.r0 * sn[q], T2.y, T2.w)) : T2.w;
+      const float ox = R0 ? fmaf(S.r0 * cs[q], T0.x, fmaf(S.r0 * sn[q], T0.y, T0.w)) : A.w;
+      const float oy = R0 ? fmaf(S.r0 * cs[q], T1.x, fmaf(S.r0 * sn[q], T1.y, T1.w)) : B.w;
+      const float oz = R0 ? fmaf(S.r0 * cs[q], T2.x, fmaf(S.r0 * sn[q], T2.y, T2.w)) : C.w;
       const float X = fmaf(r, Dx, ox);
       const float Y = fmaf(r, Dy, oy);
       const float Z = fmaf(r, Dz, oz);
@@ -577,6 +611,8 @@ __global__ void __launch_bounds__(THREADS, RIMG_ICP_THREADS_PER_SM / THREADS) k_
   icp_prefetch<THREADS>(a, sm, pair, v_begin, v_end);
   if (tid < 12) reinterpret_cast<float*>(sm.T4)[tid] = (float)a.pose[pair * 16 + tid];
   __syncthreads();
+  icp_row_table(a.src, sm, v_begin, max(0, v_end - v_begin));
+  __syncthreads();
   icp_block_terms<R0, GATE, ASSOC, KAHAN, THREADS, ROWSTRIDE, FAST>(a, sm, pair, v_begin, v_end, true);
   if (a.bpp == 1) {
     // one block per pair: the block total is the pair total
@@ -669,6 +705,8 @@ __global__ void __launch_bounds__(THREADS, RIMG_ICP_THREADS_PER_SM / THREADS) k_
   if (tid == 0) degenerate = 0;
   __syncthreads();
   for (int it = 0; it < iters; ++it) {
+    icp_row_table(a.src, sm, 0, a.src.H);
+    __syncthreads();
     icp_block_terms<R0, GATE, false, KAHAN, THREADS, ROWSTRIDE, FAST>(a, sm, pair, 0, a.src.H);
     if (tid < kRed) sm.tot[tid] = (double)block_total(sm, tid);
     __syncthreads();
@@ -758,6 +796,8 @@ __global__ void __launch_bounds__(kQueueThreads, RIMG_ICP_THREADS_PER_SM / kQueu
       __syncthreads();
       const int iters = iters_s;
       for (int it = 0; it < iters; ++it) {
+        icp_row_table(la.src, sm, 0, la.src.H);
+        __syncthreads();
         icp_block_terms<R0, false, false, KAHAN, THREADS, true, true>(la, sm, pair, 0, la.src.H);
         if (tid < kRed) sm.tot[tid] = (double)block_total<THREADS>(sm, tid);
         __syncthreads();
@@ -787,7 +827,8 @@ namespace {
 template <bool R0, bool KAHAN>
 cudaError_t launch_queue_t(const QueueGroup* dev_groups, int n_groups, int n_items, unsigned* counter,
                            cudaStream_t st) {
-  constexpr size_t bytes = sizeof(IcpSmem<kQueueThreads>);
+  // every queued level fits one block (icp_iters_fits), so at most kMaxBlockRows rows
+  constexpr size_t bytes = icp_smem_bytes<kQueueThreads>(kMaxBlockRows);
   static int grid_cap = 0;     // resident blocks on the device (per instantiation)
   if (grid_cap == 0) {
     cudaError_t e = cudaFuncSetAttribute(k_icp_queue<R0, KAHAN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -835,9 +876,9 @@ int g_blocks_per_sm[2] = {0, 0};   // resident blocks per SM for 128- and 256-th
 
 template <int T>
 int occupancy() {
-  constexpr size_t bytes = sizeof(IcpSmem<T>);
+  constexpr size_t bytes = icp_smem_bytes<T>(16);   // a typical block's row table
   cudaFuncSetAttribute(k_icp<false, false, false, true, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)bytes);
+                       (int)icp_smem_bytes<T>(kMaxBlockRows));
   int nb = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_icp<false, false, false, true, T>, T, bytes);
   return nb > 0 ? nb : 1;
@@ -941,11 +982,12 @@ inline bool fast_projection(const IcpLaunch& a) {
 
 template <bool R0, bool GATE, bool ASSOC, bool KAHAN, int T, bool ROWSTRIDE, bool FAST = false>
 cudaError_t launch_icp_ts(const IcpLaunch& a, long long blocks, cudaStream_t st) {
-  constexpr size_t bytes = sizeof(IcpSmem<T>);
+  const size_t bytes = icp_smem_bytes<T>(a.rows_per_block);
   static bool configured = false;   // per instantiation; the attribute is per function
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(k_icp<R0, GATE, ASSOC, KAHAN, T, ROWSTRIDE, FAST>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)icp_smem_bytes<T>(kMaxBlockRows));
     if (e != cudaSuccess) return e;
     configured = true;
   }
@@ -976,11 +1018,12 @@ cudaError_t launch_icp_k(const IcpLaunch& a, long long blocks, cudaStream_t st) 
 
 template <bool R0, bool GATE, bool KAHAN, int T, bool ROWSTRIDE, bool FAST = false>
 cudaError_t launch_icp_iters_ts(const IcpLaunch& a, int iters, cudaStream_t st) {
-  constexpr size_t bytes = sizeof(IcpSmem<T>);
+  const size_t bytes = icp_smem_bytes<T>(a.src.H);
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(k_icp_iters<R0, GATE, KAHAN, T, ROWSTRIDE, FAST>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)icp_smem_bytes<T>(kMaxBlockRows));
     if (e != cudaSuccess) return e;
     configured = true;
   }
@@ -1005,7 +1048,7 @@ cudaError_t launch_icp_iters_k(const IcpLaunch& a, int iters, cudaStream_t st) {
                           : launch_icp_iters_t<R0, GATE, KAHAN, 256>(a, iters, st);
 }
 
-bool icp_iters_fits(int H, int W) { return (long long)H * (W / 4) <= kIcpItersMaxChunks; }
+bool icp_iters_fits(int H, int W) { return H <= kMaxBlockRows && (long long)H * (W / 4) <= kIcpItersMaxChunks; }
 
 cudaError_t launch_icp_iters(IcpLaunch a, int iters, cudaStream_t st) {
   if (a.n_pairs == 0 || iters == 0) return cudaSuccess;
@@ -1024,8 +1067,12 @@ cudaError_t launch_icp_iters(IcpLaunch a, int iters, cudaStream_t st) {
   return kahan ? launch_icp_iters_k<false, false, true>(a, iters, st) : launch_icp_iters_k<false, false, false>(a, iters, st);
 }
 
-cudaError_t launch_icp(const IcpLaunch& a, cudaStream_t st) {
+cudaError_t launch_icp(IcpLaunch a, cudaStream_t st) {
   if (a.n_pairs == 0) return cudaSuccess;
+  if (a.rows_per_block > kMaxBlockRows) {   // the row table bounds a block's rows
+    a.rows_per_block = kMaxBlockRows;
+    a.bpp = (a.src.H + kMaxBlockRows - 1) / kMaxBlockRows;
+  }
   const long long blocks = (long long)a.n_pairs * a.bpp;
   const bool r0 = a.dst.r0 != 0.f || a.src.r0 != 0.f;
   const bool gate = a.max_corr_dist > 0.f;

@@ -66,7 +66,7 @@ void icp_tune_erase(int H, int W, int n_pairs);
 void icp_sched_set(int H, int W, int n_pairs, bool fused);
 bool icp_sched_fused(int H, int W, int n_pairs);
 int icp_tune_size();
-cudaError_t launch_icp(const IcpLaunch& a, cudaStream_t st);
+cudaError_t launch_icp(IcpLaunch a, cudaStream_t st);
 cudaError_t launch_solve(int n_pairs, double* sums, double* pose, int* status, cudaStream_t st);
 // All iterations of a level whose pair fits one block (H_l * W_l / 4 chunks
 // <= kIcpItersMaxChunks, i.e. at most 16 chunks per thread of a 256-thread
