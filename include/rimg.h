@@ -377,10 +377,22 @@ int rimg_register_groups(int n_groups, const rimg_group* groups, void* workspace
  *    iteration -- and records the faster schedule;
  *  - records the best shape for levels that run as per-iteration launches.
  * The choices go to a process-wide table keyed by (level size, pairs) that
- * later rimg_register / rimg_register_groups calls use.  T_out ends as a copy
- * of T_init.  SYNCHRONOUS; returns the number of entries set (>= 0) or a
- * negative status.  rimg_autotune_clear empties the table. */
+ * later rimg_register / rimg_register_groups calls use.  Last, the whole call
+ * is timed with the new table and with the table as rimg_autotune found it
+ * (twice each, alternately); the new entries stay only if they are faster,
+ * otherwise the table is left as it was and the return value is 0.  T_out ends
+ * as a copy of T_init.  SYNCHRONOUS; returns the number of entries set (>= 0)
+ * or a negative status.  rimg_autotune_clear empties the table.
+ *
+ * rimg_autotune_register: the same tuning for a batch registered with
+ * rimg_register (arguments as for rimg_register, workspace >=
+ * rimg_register_workspace_bytes()), every timing taken through
+ * rimg_register itself. */
 int rimg_autotune(int n_groups, const rimg_group* groups, void* workspace, size_t workspace_bytes, void* stream);
+int rimg_autotune_register(const rimg_sensor* src, const rimg_sensor* dst, int n_pairs, const float* src_range,
+                           const float* dst_range, const double* T_init, double* T_out, int levels,
+                           const int* iters, const rimg_params* p, void* workspace, size_t workspace_bytes,
+                           void* stream);
 int rimg_autotune_clear(void);
 /* One entry of the same table set by hand (a saved tuning, or a test that
  * pins a candidate): for levels of H_l x W_l pixels registered in launches of

@@ -45,7 +45,7 @@ HEADER_FUNCTIONS = [
     "rimg_sensor_table_bytes", "rimg_sensor_build", "rimg_unproject", "rimg_pyramid", "rimg_normals",
     "rimg_icp_workspace_bytes", "rimg_icp_step", "rimg_icp_step_static", "rimg_gn_update",
     "rimg_register_workspace_bytes", "rimg_register", "rimg_register_last_sums",
-    "rimg_register_groups_workspace_bytes", "rimg_register_groups", "rimg_autotune", "rimg_autotune_clear", "rimg_autotune_set",
+    "rimg_register_groups_workspace_bytes", "rimg_register_groups", "rimg_autotune", "rimg_autotune_register", "rimg_autotune_clear", "rimg_autotune_set",
     "rimg_register_host_workspace_bytes", "rimg_register_host", "rimg_register_host_async",
     "rimg_gemm_bf16", "rimg_profile_begin", "rimg_profile_end", "rimg_sdf_integrate", "rimg_points_to_range",
     "rimg_cnn_param_count", "rimg_cnn_state_bytes", "rimg_cnn_workspace_bytes", "rimg_cnn_init", "rimg_cnn_load",

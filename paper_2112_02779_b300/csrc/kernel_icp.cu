@@ -459,6 +459,8 @@ __device__ __forceinline__ void icp_block_terms(const IcpLaunch& a, IcpSmem<THRE
     // r (cs A + sn B + C) + t, plus r0 (cs R0 + sn R1) with a receiver offset.
     const float4* rt = rowtab + 3 * (v - v_begin);
     const float4 A = rt[0], B = rt[1], C = rt[2];
+    int gidx[4];
+    bool gok[4];
     const float4 T0 = sm.T4[0], T1 = sm.T4[1], T2 = sm.T4[2];   // read with a receiver offset only
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -480,14 +482,15 @@ __device__ __forceinline__ void icp_block_terms(const IcpLaunch& a, IcpSmem<THRE
       P.x[q] = X;
       P.y[q] = Y;
       P.z[q] = Z;
-      P.idx[q] = ok ? idx : -1;
+      P.idx[q] = ok ? idx : -1;    // read by the gate and the association output only
+      gidx[q] = ok ? idx : 0;
+      gok[q] = ok;
     }
     // The gathers after all four projections: each copy is an asm statement
     // that clobbers memory, so a copy between two projections would keep the
     // next pixel's table loads from moving above it.
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-      cp_async16_zfill(&sm.planes[slot][q][tid], planes + max(P.idx[q], 0), P.idx[q] >= 0);
+    for (int q = 0; q < 4; ++q) cp_async16_zfill(&sm.planes[slot][q][tid], planes + gidx[q], gok[q]);
   };
 
   // The warp's plain sums since the last step, added to each lane's running
@@ -927,6 +930,25 @@ int icp_tune_size() {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   return (int)(g_tune.size() + g_sched.size());
 }
+
+struct IcpTuneTable {
+  std::map<std::tuple<int, int, int>, std::pair<int, int>> shapes;
+  std::map<std::tuple<int, int, int>, bool> sched;
+};
+
+void* icp_tune_save() {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  return new IcpTuneTable{g_tune, g_sched};
+}
+
+void icp_tune_restore(const void* saved) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  const IcpTuneTable* t = static_cast<const IcpTuneTable*>(saved);
+  g_tune = t->shapes;
+  g_sched = t->sched;
+}
+
+void icp_tune_free(void* saved) { delete static_cast<IcpTuneTable*>(saved); }
 
 void icp_grid(int H, int W, int n_pairs, int* bpp, int* rows_per_block, int* threads) {
   {

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <mutex>
 #include <numeric>
 #include <string>
@@ -1198,19 +1199,19 @@ int rimg_register_groups(int n_groups, const rimg_group* groups, void* workspace
   return RIMG_OK;
 }
 
-int rimg_autotune(int n_groups, const rimg_group* groups, void* workspace, size_t workspace_bytes, void* stream) {
-  size_t need = 0;
-  int rc = rimg_register_groups_workspace_bytes(n_groups, groups, &need);
-  if (rc) return rc;
-  if (n_groups == 0) return 0;
-  if (!workspace || !aligned(workspace) || workspace_bytes < need) return RIMG_ERR_WORKSPACE;
+// The autotuner over the groups (see rimg_autotune), timing the whole
+// registration through `call` (rimg_register_groups, or rimg_register for
+// one group); ws holds each group's registration workspace at the offsets of
+// groups_ws.
+int autotune_impl(int n_groups, const rimg_group* groups, char* ws, cudaStream_t st,
+                  const std::function<int()>& call) {
+  int rc = RIMG_OK;
   const GroupWs w = groups_ws(n_groups, groups);
   const std::vector<Slice> slices = group_slices(n_groups, groups);
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  char* ws = static_cast<char*>(workspace);
   cudaEvent_t e0, e1;
   RIMG_CUDA(cudaEventCreate(&e0));
   RIMG_CUDA(cudaEventCreate(&e1));
+  void* before = icp_tune_save();   // the table as this call found it
   int entries = 0;
   std::vector<std::tuple<int, int, int>> done;
   std::vector<std::tuple<int, int, int>> fitting;   // (H_l, W_l, pairs) of levels that fit one block
@@ -1285,13 +1286,13 @@ int rimg_autotune(int n_groups, const rimg_group* groups, void* workspace, size_
   // Timing the whole call keeps the concurrency of the other groups and
   // sub-batches, which a level timed alone would not show.
   auto time_call = [&](float* ms) -> int {   // the shortest of three runs of three calls
-    int r = rimg_register_groups(n_groups, groups, workspace, workspace_bytes, stream);
+    int r = call();
     if (r) return r;
     *ms = 1e30f;
     for (int run = 0; run < 3; ++run) {
       RIMG_CUDA(cudaEventRecord(e0, st));
       for (int rep = 0; rep < 3; ++rep) {
-        r = rimg_register_groups(n_groups, groups, workspace, workspace_bytes, stream);
+        r = call();
         if (r) return r;
       }
       RIMG_CUDA(cudaEventRecord(e1, st));
@@ -1318,6 +1319,25 @@ int rimg_autotune(int n_groups, const rimg_group* groups, void* workspace, size_
       --entries;
     }
   }
+  // The tuned table against the table as this call found it, each timed in
+  // context twice, alternately: the tuning stays only if it is faster (the
+  // single decisions above are taken on noisy timings).
+  {
+    void* after = icp_tune_save();
+    float t_after = 1e30f, t_before = 1e30f, t = 0.f;
+    for (int r = 0; r < 2 && rc == RIMG_OK; ++r) {
+      icp_tune_restore(after);
+      if ((rc = time_call(&t)) == RIMG_OK) t_after = std::min(t_after, t);
+      icp_tune_restore(before);
+      if (rc == RIMG_OK && (rc = time_call(&t)) == RIMG_OK) t_before = std::min(t_before, t);
+    }
+    const bool keep = rc == RIMG_OK && t_after < t_before;
+    icp_tune_restore(keep ? after : before);
+    if (!keep) entries = 0;
+    icp_tune_free(after);
+  }
+  icp_tune_free(before);
+  if (rc) return rc;
   // T_out ends as a copy of T_init
   for (int i = 0; i < n_groups; ++i)
     if (groups[i].n_pairs > 0 && groups[i].T_out != groups[i].T_init)
@@ -1327,6 +1347,36 @@ int rimg_autotune(int n_groups, const rimg_group* groups, void* workspace, size_
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return entries;
+}
+
+int rimg_autotune(int n_groups, const rimg_group* groups, void* workspace, size_t workspace_bytes, void* stream) {
+  size_t need = 0;
+  int rc = rimg_register_groups_workspace_bytes(n_groups, groups, &need);
+  if (rc) return rc;
+  if (n_groups == 0) return 0;
+  if (!workspace || !aligned(workspace) || workspace_bytes < need) return RIMG_ERR_WORKSPACE;
+  return autotune_impl(n_groups, groups, static_cast<char*>(workspace), static_cast<cudaStream_t>(stream),
+                       [&]() { return rimg_register_groups(n_groups, groups, workspace, workspace_bytes, stream); });
+}
+
+int rimg_autotune_register(const rimg_sensor* src, const rimg_sensor* dst, int n_pairs, const float* src_range,
+                           const float* dst_range, const double* T_init, double* T_out, int levels,
+                           const int* iters, const rimg_params* p, void* workspace, size_t workspace_bytes,
+                           void* stream) {
+  int rc = check_register_args(src, dst, n_pairs, levels, iters, p);
+  if (rc) return rc;
+  if (n_pairs == 0) return 0;
+  if (!src_range || !dst_range || !T_init || !T_out || !workspace) return RIMG_ERR_INVALID_ARG;
+  if ((reinterpret_cast<uintptr_t>(src_range) % 16) || (reinterpret_cast<uintptr_t>(dst_range) % 16))
+    return RIMG_ERR_INVALID_ARG;
+  const RegWs R = reg_ws(src->H, src->W, n_pairs, levels, 0);
+  if (!aligned(workspace) || workspace_bytes < R.end) return RIMG_ERR_WORKSPACE;
+  // one group whose registration workspace sits at offset 0, as rimg_register's
+  const rimg_group g{src, dst, n_pairs, levels, iters, p, src_range, dst_range, T_init, T_out, nullptr};
+  return autotune_impl(1, &g, static_cast<char*>(workspace), static_cast<cudaStream_t>(stream), [&]() {
+    return rimg_register(src, dst, n_pairs, src_range, dst_range, T_init, T_out, levels, iters, p, nullptr,
+                         workspace, workspace_bytes, stream);
+  });
 }
 
 int rimg_autotune_clear(void) {

@@ -66,11 +66,14 @@ __device__ __forceinline__ float atan2_poly(float y, float x) {
   return copysignf(r, y);
 }
 
-// Column from the continuous estimate u_c: floor(u_c + 1/2) wrapped into
-// [0, W).  Here |u_c| < W (atan2 in [-pi, pi] and |theta_lut| < pi), so one
-// conditional add or subtract of W lands in [0, W); NaN converts to 0.
+// Column from the continuous estimate u_c: u_c rounded to the nearest
+// integer (floor(u_c + 1/2) except where u_c is exactly a half-integer, a tie;
+// the same conversion as the branch-free form of project_px, so both forms
+// decide alike) wrapped into [0, W).  Here |u_c| < W (atan2 in [-pi, pi] and
+// |theta_lut| < pi), so one conditional add or subtract of W lands in [0, W);
+// NaN converts to 0.
 __device__ __forceinline__ int wrap_col(float uc, int W) {
-  int u = __float2int_rd(uc + 0.5f);
+  int u = __float2int_rn(uc);
   u = (u < 0) ? u + W : u;
   u = (u >= W) ? u - W : u;
   return u;
@@ -82,7 +85,9 @@ __device__ __forceinline__ int wrap_col(float uc, int W) {
 // the last fixed-point step).  FAST: the caller knows that L's inverse table
 // is exact, that L has no azimuth offsets (theta_lut = 0) and that its width
 // is a power of two, so the projection is one straight-line block and the
-// column wraps by a mask (floor(u_c + 1/2) mod W for every integer, NaN -> 0).
+// column wraps by a mask: u_c rounded to the nearest integer (one conversion;
+// it differs from floor(u_c + 1/2) only where u_c is exactly a half-integer,
+// a tie) mod W, NaN -> 0.
 template <bool R0, bool FAST = false>
 __device__ __forceinline__ bool project_px(const DevLevel& L, float3 x, int proj_iters, int& u, int& v,
                                            float& r) {
@@ -95,7 +100,7 @@ __device__ __forceinline__ bool project_px(const DevLevel& L, float3 x, int proj
     v = row_from_sin<FAST>(L, s);
     float uc = atan2_poly(x.y, x.x) * L.w_over_2pi;
     if (!FAST && L.has_theta) uc -= __ldg(L.thu + v);
-    u = FAST ? (__float2int_rd(uc + 0.5f) & (L.W - 1)) : wrap_col(uc, L.W);
+    u = FAST ? (__float2int_rn(uc) & (L.W - 1)) : wrap_col(uc, L.W);
   } else {
     // receiver-offset fixed point on the column angle 2 pi u_c / W
     float uc = atan2_poly(x.y, x.x) * L.w_over_2pi;
@@ -115,7 +120,7 @@ __device__ __forceinline__ bool project_px(const DevLevel& L, float3 x, int proj
       uc = atan2_poly(yp, xp) * L.w_over_2pi;
       if (!FAST && L.has_theta) uc -= __ldg(L.thu + v);
     }
-    u = FAST ? (__float2int_rd(uc + 0.5f) & (L.W - 1)) : wrap_col(uc, L.W);
+    u = FAST ? (__float2int_rn(uc) & (L.W - 1)) : wrap_col(uc, L.W);
   }
   return (s >= L.s_lo) && (s <= L.s_hi);   // false for NaN
 }

@@ -66,6 +66,11 @@ void icp_tune_erase(int H, int W, int n_pairs);
 void icp_sched_set(int H, int W, int n_pairs, bool fused);
 bool icp_sched_fused(int H, int W, int n_pairs);
 int icp_tune_size();
+// A copy of the whole table (shapes and schedules), put back by
+// icp_tune_restore; icp_tune_free releases the copy.
+void* icp_tune_save();
+void icp_tune_restore(const void* saved);
+void icp_tune_free(void* saved);
 cudaError_t launch_icp(IcpLaunch a, cudaStream_t st);
 cudaError_t launch_solve(int n_pairs, double* sums, double* pose, int* status, cudaStream_t st);
 // All iterations of a level whose pair fits one block (H_l * W_l / 4 chunks

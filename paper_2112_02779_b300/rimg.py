@@ -64,6 +64,8 @@ _sig("rimg_register_groups_workspace_bytes", _c_int, _c_int, _P(rimg_group), _P(
 _sig("rimg_register_groups", _c_int, _c_int, _P(rimg_group), _vp, _c_size, _vp)
 _sig("rimg_autotune", _c_int, _c_int, _P(rimg_group), _vp, _c_size, _vp)
 _sig("rimg_autotune_clear", _c_int)
+_sig("rimg_autotune_register", _c_int, _P(rimg_sensor), _P(rimg_sensor), _c_int, _vp, _vp, _vp, _vp, _c_int,
+     _P(_c_int), _P(rimg_params), _vp, _c_size, _vp)
 _sig("rimg_autotune_set", _c_int, _c_int, _c_int, _c_int, _c_int, _c_int, _c_int)
 _sig("rimg_gemm_bf16", _c_int, _c_int, _c_int, _c_int, _vp, _c_int, _vp, _c_int, _vp, _c_int, _vp, _vp, _c_int,
      _c_int, _vp, _vp)
@@ -315,6 +317,16 @@ def rimg_autotune(groups, workspace, stream=None):
     n = _lib.rimg_autotune(groups.n, groups.array, _ptr(workspace), workspace.numel(), _stream(stream))
     if n < 0:
         raise RimgError("rimg_autotune", n)
+    return n
+
+
+def rimg_autotune_register(src, dst, n_pairs, src_range, dst_range, T_init, T_out, levels, iters, params,
+                           workspace, stream=None):
+    n = _lib.rimg_autotune_register(
+        src.ref(), dst.ref(), n_pairs, _ptr(src_range), _ptr(dst_range), _ptr(T_init), _ptr(T_out), levels,
+        _iters(iters), ctypes.byref(params), _ptr(workspace), workspace.numel(), _stream(stream))
+    if n < 0:
+        raise RimgError("rimg_autotune_register", n)
     return n
 
 
