@@ -297,17 +297,16 @@ __device__ __forceinline__ float4* row_table(IcpSmem<THREADS>& sm) {
   return reinterpret_cast<float4*>(reinterpret_cast<char*>(&sm) + row_table_offset<THREADS>());
 }
 
-// Fills the row table for rows [v_begin, v_begin + nrows) of level S at the
-// pose in sm.T4.  With the row's cos/sin of elevation and azimuth offset and
-// the rotation columns R0, R1, R2,
+// Fills rows i = first, first + step, ... < nrows of the row table for rows
+// [v_begin, v_begin + nrows) of level S at the FP32 pose rows T0, T1, T2
+// (R | t).  With the row's cos/sin of elevation and azimuth offset and the
+// rotation columns R0, R1, R2,
 //   R p = r (cos u A + sin u B + C),  A = cos(phi) (cos(th) R0 + sin(th) R1),
 //   B = cos(phi) (cos(th) R1 - sin(th) R0),  C = sin(phi) R2.
-// The caller synchronises the block before the table is read.
-template <int THREADS>
-__device__ __forceinline__ void icp_row_table(const DevLevel& S, IcpSmem<THREADS>& sm, int v_begin, int nrows) {
-  float4* rt = row_table(sm);
-  const float4 T0 = sm.T4[0], T1 = sm.T4[1], T2 = sm.T4[2];
-  for (int i = threadIdx.x; i < nrows; i += THREADS) {
+// The block is synchronised before the table is read.
+__device__ __forceinline__ void fill_row_table(const DevLevel& S, float4* rt, float4 T0, float4 T1, float4 T2,
+                                               int v_begin, int nrows, int first, int step) {
+  for (int i = first; i < nrows; i += step) {
     const float4 rw = __ldg(S.rows + v_begin + i);
     const float q0 = rw.x * rw.z, q1 = rw.x * rw.w;
     rt[3 * i] = make_float4(fmaf(q0, T0.x, q1 * T0.y), fmaf(q0, T1.x, q1 * T1.y), fmaf(q0, T2.x, q1 * T2.y), T0.w);
@@ -315,6 +314,15 @@ __device__ __forceinline__ void icp_row_table(const DevLevel& S, IcpSmem<THREADS
                                 T1.w);
     rt[3 * i + 2] = make_float4(rw.y * T0.z, rw.y * T1.z, rw.y * T2.z, T2.w);
   }
+}
+
+// The row table from the pose in sm.T4, by all threads of the block (the
+// caller synchronised after writing sm.T4) or by one warp (lane = its lane,
+// after the warp wrote sm.T4; step 32).
+template <int THREADS>
+__device__ __forceinline__ void icp_row_table(const DevLevel& S, IcpSmem<THREADS>& sm, int v_begin, int nrows,
+                                              int first, int step) {
+  fill_row_table(S, row_table(sm), sm.T4[0], sm.T4[1], sm.T4[2], v_begin, nrows, first, step);
 }
 
 // Chunks summed plainly per thread between two compensated warp steps.
@@ -614,7 +622,9 @@ __global__ void __launch_bounds__(THREADS, RIMG_ICP_THREADS_PER_SM / THREADS) k_
   icp_prefetch<THREADS>(a, sm, pair, v_begin, v_end);
   if (tid < 12) reinterpret_cast<float*>(sm.T4)[tid] = (float)a.pose[pair * 16 + tid];
   __syncthreads();
-  icp_row_table(a.src, sm, v_begin, max(0, v_end - v_begin));
+  // (filling the table straight from the pose in global memory, with one
+  // barrier less, measured slower)
+  icp_row_table(a.src, sm, v_begin, max(0, v_end - v_begin), tid, THREADS);
   __syncthreads();
   icp_block_terms<R0, GATE, ASSOC, KAHAN, THREADS, ROWSTRIDE, FAST>(a, sm, pair, v_begin, v_end, true);
   if (a.bpp == 1) {
@@ -707,9 +717,9 @@ __global__ void __launch_bounds__(THREADS, RIMG_ICP_THREADS_PER_SM / THREADS) k_
   }
   if (tid == 0) degenerate = 0;
   __syncthreads();
+  icp_row_table(a.src, sm, 0, a.src.H, tid, THREADS);
+  __syncthreads();
   for (int it = 0; it < iters; ++it) {
-    icp_row_table(a.src, sm, 0, a.src.H);
-    __syncthreads();
     icp_block_terms<R0, GATE, false, KAHAN, THREADS, ROWSTRIDE, FAST>(a, sm, pair, 0, a.src.H);
     if (tid < kRed) sm.tot[tid] = (double)block_total(sm, tid);
     __syncthreads();
@@ -717,6 +727,11 @@ __global__ void __launch_bounds__(THREADS, RIMG_ICP_THREADS_PER_SM / THREADS) k_
       const bool ok = warp_gn_update(sm.tot, Tp, reinterpret_cast<float*>(sm.T4), it == iters - 1 ? sm.tot + 29 : nullptr,
                                      tid);
       if (!ok && tid == 0) degenerate = 1;
+      // the next iteration's row table, by the warp that updated the pose
+      if (it + 1 < iters) {
+        __syncwarp();
+        icp_row_table(a.src, sm, 0, a.src.H, tid, 32);
+      }
     }
     __syncthreads();
   }
@@ -798,9 +813,11 @@ __global__ void __launch_bounds__(kQueueThreads, RIMG_ICP_THREADS_PER_SM / kQueu
       }
       __syncthreads();
       const int iters = iters_s;
-      for (int it = 0; it < iters; ++it) {
-        icp_row_table(la.src, sm, 0, la.src.H);
+      if (iters > 0) {
+        icp_row_table(la.src, sm, 0, la.src.H, tid, THREADS);
         __syncthreads();
+      }
+      for (int it = 0; it < iters; ++it) {
         icp_block_terms<R0, false, false, KAHAN, THREADS, true, true>(la, sm, pair, 0, la.src.H);
         if (tid < kRed) sm.tot[tid] = (double)block_total<THREADS>(sm, tid);
         __syncthreads();
@@ -809,6 +826,11 @@ __global__ void __launch_bounds__(kQueueThreads, RIMG_ICP_THREADS_PER_SM / kQueu
           const bool ok = warp_gn_update(sm.tot, Tp, reinterpret_cast<float*>(sm.T4), last ? sm.tot + 29 : nullptr,
                                          tid);
           if (!ok && tid == 0) degenerate = 1;
+          // the next iteration's row table, by the warp that updated the pose
+          if (it + 1 < iters) {
+            __syncwarp();
+            icp_row_table(la.src, sm, 0, la.src.H, tid, 32);
+          }
         }
         __syncthreads();
         ran = true;
