@@ -74,7 +74,7 @@ void icp_tune_free(void* saved);
 cudaError_t launch_icp(IcpLaunch a, cudaStream_t st);
 cudaError_t launch_solve(int n_pairs, double* sums, double* pose, int* status, cudaStream_t st);
 // All iterations of a level whose pair fits one block (H_l * W_l / 4 chunks
-// <= kIcpItersMaxChunks, i.e. at most 16 chunks per thread of a 256-thread
+// <= kIcpItersMaxChunks, i.e. at most 32 chunks per thread of a 128-thread
 // block) in one launch; a.pose is updated in place.
 constexpr int kIcpItersMaxChunks = 4096;
 bool icp_iters_fits(int H, int W);
@@ -105,7 +105,10 @@ struct QueueGroup {
   double* sums;                       // [n][32], the last step's sums and step record
   int* status;                        // [n] or null
 };
-constexpr int kQueueThreads = 256;
+#ifndef RIMG_QUEUE_THREADS
+#define RIMG_QUEUE_THREADS 256
+#endif
+constexpr int kQueueThreads = RIMG_QUEUE_THREADS;
 // Whether level (H, W) runs in the queue kernel: it fits one block and its
 // chunks per row divide the block (row-stride cursors).
 bool queue_level_ok(int H, int W);
