@@ -370,11 +370,15 @@ int rimg_register_groups(int n_groups, const rimg_group* groups, void* workspace
  * workspace and, on the group's own data, for every level:
  *  - times every candidate shape of the association kernel (threads per
  *    block, blocks per pair) without updating poses;
- *  - where the level's pair fits one block, times its whole iteration count
- *    both ways -- all iterations in one block per pair (the persistent queue
- *    of rimg_register_groups / the one-launch level of rimg_register) and one
- *    association launch of the best shape plus one FP64 solve launch per
- *    iteration -- and records the faster schedule;
+ *  - where the level's pair fits one block, and on every level of
+ *    sub-batches of at most 64 pairs, times its whole iteration count each
+ *    way -- all iterations in one block per pair (where the pair fits one
+ *    block: the persistent queue of rimg_register_groups / the one-launch
+ *    level of rimg_register), one association launch of the best shape plus
+ *    one FP64 solve launch per iteration, and all iterations on a
+ *    thread-block cluster of 2, 4 or 8 blocks per pair (one launch; the
+ *    blocks exchange their sums through distributed shared memory, one
+ *    cluster barrier per iteration) -- and records the fastest schedule;
  *  - records the best shape for levels that run as per-iteration launches.
  * The choices go to a process-wide table keyed by (level size, pairs) that
  * later rimg_register / rimg_register_groups calls use.  Last, the whole call
@@ -400,10 +404,15 @@ int rimg_autotune_clear(void);
  * 256; 0 removes the shape entry) and blocks per pair (1 .. H_l, rounded as
  * the tuner rounds: whole rows per block) -- and the schedule: 1 all
  * iterations in one block per pair (taken only where the pair fits one
- * block), 0 one association launch and one FP64 solve launch per iteration,
- * -1 leaves the schedule entry as it is.  Returns RIMG_OK or
- * RIMG_ERR_INVALID_ARG (non-positive sizes, other thread counts, blocks per
- * pair outside 1 .. H_l, schedule outside -1 .. 1). */
+ * block, else 0), 2, 4 or 8 all iterations on a cluster of that many
+ * 128-thread blocks per pair (any level; with the distance gate a cluster
+ * schedule runs as 1 where the pair fits one block, else as 0), 0 one
+ * association launch and one FP64 solve launch per iteration, -1 leaves the
+ * schedule entry as it is.  A cluster of C blocks gives the same poses and
+ * sums, bit for bit, as per-iteration launches with 128 threads and C blocks
+ * per pair.  Returns RIMG_OK or RIMG_ERR_INVALID_ARG (non-positive sizes,
+ * other thread counts, blocks per pair outside 1 .. H_l, schedule not one of
+ * -1, 0, 1, 2, 4, 8). */
 int rimg_autotune_set(int H_l, int W_l, int n_pairs, int threads, int blocks_per_pair, int schedule);
 
 /* ---------------------------------------------------------------------------

@@ -13,6 +13,8 @@
 #include <tuple>
 #include <utility>
 
+#include <cooperative_groups.h>
+
 #include "rimg_device.cuh"
 
 namespace rimg {
@@ -740,6 +742,79 @@ __global__ void __launch_bounds__(THREADS, RIMG_ICP_THREADS_PER_SM / THREADS) k_
   if (tid == 0 && degenerate && a.status) a.status[pair] |= RIMG_FLAG_DEGENERATE;
 }
 
+// All iterations of one small level in one launch, each pair on a cluster of
+// C blocks (thread-block cluster, distributed shared memory): block r of the
+// cluster takes rows [r * rpb, (r + 1) * rpb) of the pair (rpb = ceil(H / C)),
+// the blocks' FP32 totals are exchanged through distributed shared memory
+// after one cluster barrier per iteration, and every block sums them in FP64
+// in rank order and runs the same FP64 update, so all blocks of a cluster
+// carry the same pose without a second barrier.  Same arithmetic, in the same
+// order, as k_icp with C blocks per pair (its last-block FP64 sum) followed by
+// k_solve: poses and sums are bit-identical to that per-iteration schedule.
+// The per-iteration latency of a pair (association, reduction, the update's
+// FP64 chain) is spread over C SMs instead of one.  The block totals are
+// double-buffered by iteration parity: a block writes buffer it % 2 again in
+// iteration it + 2, after passing the barrier of iteration it + 1, which no
+// block reaches before it has finished reading the buffers of iteration it.
+// So one cluster barrier per iteration and one before exit (no block leaves
+// while another may still read its shared memory) suffice; every block of a
+// cluster runs the same number of iterations, so every barrier completes.
+namespace cg = cooperative_groups;
+
+template <bool R0, bool KAHAN, int THREADS, bool ROWSTRIDE, bool FAST, int C>
+__global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(THREADS, RIMG_ICP_THREADS_PER_SM / THREADS)
+    k_icp_cluster(IcpLaunch a, int iters) {
+  extern __shared__ float4 smem_raw[];
+  IcpSmem<THREADS>& sm = *reinterpret_cast<IcpSmem<THREADS>*>(smem_raw);
+  __shared__ double Tp[12];
+  __shared__ float blk[2][32];
+  __shared__ int degenerate;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int tid = threadIdx.x;
+  const int rank = (int)cluster.block_rank();
+  const int pair = blockIdx.x / C;
+  const int rpb = (a.src.H + C - 1) / C;
+  const int v_begin = min(a.src.H, rank * rpb);
+  const int v_end = min(a.src.H, v_begin + rpb);
+  if (tid < 12) {
+    Tp[tid] = a.pose[pair * 16 + tid];
+    reinterpret_cast<float*>(sm.T4)[tid] = (float)Tp[tid];
+  }
+  if (tid == 0) degenerate = 0;
+  __syncthreads();
+  icp_row_table(a.src, sm, v_begin, v_end - v_begin, tid, THREADS);
+  __syncthreads();
+  for (int it = 0; it < iters; ++it) {
+    icp_block_terms<R0, false, false, KAHAN, THREADS, ROWSTRIDE, FAST>(a, sm, pair, v_begin, v_end);
+    float* mine = blk[it & 1];
+    if (tid < kRed) mine[tid] = block_total(sm, tid);
+    cluster.sync();
+    if (tid < kRed) {
+      double acc = 0.0;
+#pragma unroll
+      for (int r = 0; r < C; ++r) acc += (double)*cluster.map_shared_rank(mine + tid, r);
+      sm.tot[tid] = acc;
+    }
+    __syncthreads();
+    if (tid < 32) {
+      const bool ok = warp_gn_update(sm.tot, Tp, reinterpret_cast<float*>(sm.T4), it == iters - 1 ? sm.tot + 29 : nullptr,
+                                     tid);
+      if (!ok && tid == 0) degenerate = 1;
+      // the next iteration's row table, by the warp that updated the pose
+      if (it + 1 < iters) {
+        __syncwarp();
+        icp_row_table(a.src, sm, v_begin, v_end - v_begin, tid, 32);
+      }
+    }
+    __syncthreads();
+  }
+  cluster.sync();   // no block exits while another may still read its totals
+  if (rank != 0) return;
+  if (tid < 12) a.pose[pair * 16 + tid] = Tp[tid];
+  if (iters > 0 && tid < kRedStride) a.sums[pair * kRedStride + tid] = sm.tot[tid];
+  if (tid == 0 && degenerate && a.status) a.status[pair] |= RIMG_FLAG_DEGENERATE;
+}
+
 // ---------------------------------------------------------------------------
 // Persistent work queue over the small levels of uneven batches.
 
@@ -914,10 +989,11 @@ namespace {
 // Launch shapes chosen by rimg_autotune, keyed by (level rows, columns, pairs).
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int>, std::pair<int, int>> g_tune;
-// Per-level schedule chosen by rimg_autotune for levels that fit one block:
-// true = all iterations in one block per pair (k_icp_iters / the queue),
-// false = one multi-block association launch plus one solve per iteration.
-std::map<std::tuple<int, int, int>, bool> g_sched;
+// Per-level schedule chosen by rimg_autotune: 1 = all iterations in one block
+// per pair (k_icp_iters / the queue; levels that fit one block), 2, 4 or 8 =
+// all iterations on a cluster of that many blocks per pair (k_icp_cluster),
+// 0 = one multi-block association launch plus one solve per iteration.
+std::map<std::tuple<int, int, int>, int> g_sched;
 }  // namespace
 
 void icp_tune_set(int H, int W, int n_pairs, int threads, int bpp) {
@@ -936,16 +1012,18 @@ void icp_tune_erase(int H, int W, int n_pairs) {
   g_tune.erase(std::make_tuple(H, W, n_pairs));
 }
 
-void icp_sched_set(int H, int W, int n_pairs, bool fused) {
+void icp_sched_set(int H, int W, int n_pairs, int sched) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  g_sched[std::make_tuple(H, W, n_pairs)] = fused;
+  g_sched[std::make_tuple(H, W, n_pairs)] = sched;
 }
 
-bool icp_sched_fused(int H, int W, int n_pairs) {
-  if (!icp_iters_fits(H, W)) return false;
+int icp_sched(int H, int W, int n_pairs) {
+  const bool fits = icp_iters_fits(H, W);
   std::lock_guard<std::mutex> lk(g_tune_mu);
   auto it = g_sched.find(std::make_tuple(H, W, n_pairs));
-  return it == g_sched.end() ? true : it->second;
+  if (it == g_sched.end()) return fits ? 1 : 0;
+  // one block per pair only where the pair fits one block
+  return (it->second == 1 && !fits) ? 0 : it->second;
 }
 
 int icp_tune_size() {
@@ -955,7 +1033,7 @@ int icp_tune_size() {
 
 struct IcpTuneTable {
   std::map<std::tuple<int, int, int>, std::pair<int, int>> shapes;
-  std::map<std::tuple<int, int, int>, bool> sched;
+  std::map<std::tuple<int, int, int>, int> sched;
 };
 
 void* icp_tune_save() {
@@ -1093,6 +1171,52 @@ cudaError_t launch_icp_iters_k(const IcpLaunch& a, int iters, cudaStream_t st) {
 }
 
 bool icp_iters_fits(int H, int W) { return H <= kMaxBlockRows && (long long)H * (W / 4) <= kIcpItersMaxChunks; }
+
+template <bool R0, bool KAHAN, bool ROWSTRIDE, bool FAST, int C>
+cudaError_t launch_icp_cluster_ts(const IcpLaunch& a, int iters, cudaStream_t st) {
+  constexpr int T = 128;
+  const size_t bytes = icp_smem_bytes<T>(a.rows_per_block);
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_icp_cluster<R0, KAHAN, T, ROWSTRIDE, FAST, C>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)icp_smem_bytes<T>(kMaxBlockRows));
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  k_icp_cluster<R0, KAHAN, T, ROWSTRIDE, FAST, C><<<(unsigned)((long long)a.n_pairs * C), T, bytes, st>>>(a, iters);
+  return cudaGetLastError();
+}
+
+template <bool R0, bool KAHAN, int C>
+cudaError_t launch_icp_cluster_c(const IcpLaunch& a, int iters, cudaStream_t st) {
+  const bool fast = fast_projection(a);
+  if (row_stride(a, 128))
+    return fast ? launch_icp_cluster_ts<R0, KAHAN, true, true, C>(a, iters, st)
+                : launch_icp_cluster_ts<R0, KAHAN, true, false, C>(a, iters, st);
+  return fast ? launch_icp_cluster_ts<R0, KAHAN, false, true, C>(a, iters, st)
+              : launch_icp_cluster_ts<R0, KAHAN, false, false, C>(a, iters, st);
+}
+
+template <int C>
+cudaError_t launch_icp_cluster_r(const IcpLaunch& a, int iters, cudaStream_t st) {
+  const bool r0 = a.dst.r0 != 0.f || a.src.r0 != 0.f;
+  const bool kahan = a.kahan != 0;
+  if (r0) return kahan ? launch_icp_cluster_c<true, true, C>(a, iters, st) : launch_icp_cluster_c<true, false, C>(a, iters, st);
+  return kahan ? launch_icp_cluster_c<false, true, C>(a, iters, st) : launch_icp_cluster_c<false, false, C>(a, iters, st);
+}
+
+cudaError_t launch_icp_cluster(IcpLaunch a, int iters, int cluster, cudaStream_t st) {
+  if (a.n_pairs == 0 || iters == 0) return cudaSuccess;
+  if ((cluster != 2 && cluster != 4 && cluster != 8) || a.max_corr_dist > 0.f || a.assoc)
+    return cudaErrorInvalidValue;
+  a.threads = 128;
+  a.bpp = cluster;
+  a.rows_per_block = (a.src.H + cluster - 1) / cluster;
+  if (a.rows_per_block > kMaxBlockRows) return cudaErrorInvalidValue;
+  if (cluster == 2) return launch_icp_cluster_r<2>(a, iters, st);
+  return cluster == 4 ? launch_icp_cluster_r<4>(a, iters, st) : launch_icp_cluster_r<8>(a, iters, st);
+}
 
 cudaError_t launch_icp_iters(IcpLaunch a, int iters, cudaStream_t st) {
   if (a.n_pairs == 0 || iters == 0) return cudaSuccess;

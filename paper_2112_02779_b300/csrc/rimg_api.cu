@@ -240,11 +240,15 @@ int icp_launch(const rimg_sensor* src, const rimg_sensor* dst, int level, int n_
   return RIMG_OK;
 }
 
-// All `iters` Gauss-Newton steps of a small level in one launch (one block
-// per pair; see k_icp_iters).
+// All `iters` Gauss-Newton steps of a level in one launch: one block per
+// pair (k_icp_iters), or with cluster = 2, 4 or 8 a thread-block cluster of
+// that many blocks per pair (k_icp_cluster; not with the distance gate, which
+// keeps one block per pair where the pair fits one and per-iteration launches
+// elsewhere).
 int icp_iters_launch(const rimg_sensor* src, const rimg_sensor* dst, int level, int n_pairs,
                      const float* src_range_l, const float* dst_planes_l, const float* dst_range_l, double* pose,
-                     const rimg_params* p, int* status, const IcpScratch& w, int iters, cudaStream_t st) {
+                     const rimg_params* p, int* status, const IcpScratch& w, int iters, cudaStream_t st,
+                     int cluster = 1) {
   if (p->max_corr_dist > 0.f && !dst_range_l) return RIMG_ERR_INVALID_ARG;
   IcpLaunch a{};
   a.src = dev_level(src, level);
@@ -263,8 +267,17 @@ int icp_iters_launch(const rimg_sensor* src, const rimg_sensor* dst, int level, 
   a.proj_iters = p->proj_iters;
   a.kahan = p->kahan;
   a.update = 1;
-  prof_before(st, K_ICP_ITERS, level, n_pairs);
-  cudaError_t e = launch_icp_iters(a, iters, st);
+  const bool on_cluster = cluster > 1 && p->max_corr_dist <= 0.f;
+  if (!on_cluster && !icp_iters_fits(a.src.H, a.src.W)) {
+    for (int it = 0; it < iters; ++it) {
+      int rc = icp_launch(src, dst, level, n_pairs, src_range_l, dst_planes_l, dst_range_l, pose, p, 1, nullptr,
+                          nullptr, status, w, st);
+      if (rc) return rc;
+    }
+    return RIMG_OK;
+  }
+  prof_before(st, on_cluster ? K_ICP_CLUSTER : K_ICP_ITERS, level, n_pairs);
+  cudaError_t e = on_cluster ? launch_icp_cluster(a, iters, cluster, st) : launch_icp_iters(a, iters, st);
   prof_after(st);
   if (e != cudaSuccess) return cuda_fail(e, "icp iterations kernel");
   return RIMG_OK;
@@ -363,8 +376,9 @@ int slice_levels(const rimg_sensor* src, const rimg_sensor* dst, int p0, int n, 
     const int l = levels - 1 - k;
     const float* s_l = (l == 0) ? src_range : b.srcl[l];
     const float* d_l = gate ? ((l == 0) ? dst_range : b.dstl[l]) : nullptr;
-    if (iters[k] > 0 && icp_sched_fused(H >> l, W >> l, n)) {
-      int rc = icp_iters_launch(src, dst, l, n, s_l, b.planes[l], d_l, T_out, p, status, scr, iters[k], st);
+    const int sched = icp_sched(H >> l, W >> l, n);
+    if (iters[k] > 0 && sched >= 1) {
+      int rc = icp_iters_launch(src, dst, l, n, s_l, b.planes[l], d_l, T_out, p, status, scr, iters[k], st, sched);
       if (rc) return rc;
       continue;
     }
@@ -420,7 +434,7 @@ int queue_prefix_of(const rimg_sensor* src, const rimg_sensor* dst, int levels, 
     const int Hl = src->H >> l, Wl = src->W >> l;
     if (!queue_level_ok(Hl, Wl) || !fast_level(dst, l)) break;
     bool fused = true;
-    for (int n : slice_sizes) fused = fused && icp_sched_fused(Hl, Wl, n);
+    for (int n : slice_sizes) fused = fused && icp_sched(Hl, Wl, n) == 1;
     if (!fused) break;
   }
   return k;
@@ -1203,6 +1217,13 @@ int rimg_register_groups(int n_groups, const rimg_group* groups, void* workspace
 // registration through `call` (rimg_register_groups, or rimg_register for
 // one group); ws holds each group's registration workspace at the offsets of
 // groups_ws.
+// Sub-batches up to this many pairs also time cluster schedules for the
+// levels that do not fit one block (a latency gain where the batch leaves
+// the GPU room; larger batches keep per-iteration launches there).
+constexpr int kClusterTuneMaxPairs = 64;
+// A cluster block's row table holds at most this many rows.
+constexpr int kMaxRowsPerCluster = 1024;
+
 int autotune_impl(int n_groups, const rimg_group* groups, char* ws, cudaStream_t st,
                   const std::function<int()>& call) {
   int rc = RIMG_OK;
@@ -1271,7 +1292,10 @@ int autotune_impl(int n_groups, const rimg_group* groups, char* ws, cudaStream_t
       }
       icp_tune_set(Hl, Wl, sl.n, best_t, best_b);
       ++entries;
-      if (icp_iters_fits(Hl, Wl) && g.iters[k] > 0) {
+      // levels whose schedule is timed in context: those that fit one block,
+      // and in small sub-batches (clusters of blocks shorten a pair's
+      // iteration chain where the GPU has room) every level
+      if (g.iters[k] > 0 && (icp_iters_fits(Hl, Wl) || sl.n <= kClusterTuneMaxPairs)) {
         const auto key = std::make_tuple(Hl, Wl, sl.n);
         if (std::find(fitting.begin(), fitting.end(), key) == fitting.end()) fitting.push_back(key);
       }
@@ -1305,16 +1329,23 @@ int autotune_impl(int n_groups, const rimg_group* groups, char* ws, cudaStream_t
   };
   for (const auto& key : fitting) {
     const int Hl = std::get<0>(key), Wl = std::get<1>(key), n = std::get<2>(key);
-    float t_fused = 0.f, t_multi = 0.f;
-    icp_sched_set(Hl, Wl, n, true);
-    if ((rc = time_call(&t_fused))) return rc;
-    icp_sched_set(Hl, Wl, n, false);
-    if ((rc = time_call(&t_multi))) return rc;
-    const bool fused = t_fused <= t_multi;
-    icp_sched_set(Hl, Wl, n, fused);
+    // one block per pair (where the pair fits one), clusters of 2, 4 and 8
+    // blocks per pair, per-iteration launches (ties keep the earlier candidate)
+    const bool fits = icp_iters_fits(Hl, Wl);
+    float best = 1e30f;
+    int best_s = fits ? 1 : 0;
+    for (int s : {1, 0, 2, 4, 8}) {
+      if (s == 1 && !fits) continue;
+      if (s > 1 && (Hl + s - 1) / s > kMaxRowsPerCluster) continue;
+      float ms = 0.f;
+      icp_sched_set(Hl, Wl, n, s);
+      if ((rc = time_call(&ms))) return rc;
+      if (ms < best) { best = ms; best_s = s; }
+    }
+    icp_sched_set(Hl, Wl, n, best_s);
     ++entries;
     // launch shapes stay only for levels that run as per-iteration launches
-    if (fused) {
+    if (best_s != 0) {
       icp_tune_erase(Hl, Wl, n);
       --entries;
     }
@@ -1385,14 +1416,16 @@ int rimg_autotune_clear(void) {
 }
 
 int rimg_autotune_set(int H_l, int W_l, int n_pairs, int threads, int blocks_per_pair, int schedule) {
-  if (H_l <= 0 || W_l <= 0 || n_pairs <= 0 || schedule < -1 || schedule > 1) return RIMG_ERR_INVALID_ARG;
+  if (H_l <= 0 || W_l <= 0 || n_pairs <= 0 || schedule < -1 || schedule > 8 || schedule == 3 ||
+      (schedule > 4 && schedule < 8))
+    return RIMG_ERR_INVALID_ARG;
   if (threads != 0 && threads != 128 && threads != 256) return RIMG_ERR_INVALID_ARG;
   if (threads != 0 && (blocks_per_pair < 1 || blocks_per_pair > H_l)) return RIMG_ERR_INVALID_ARG;
   if (threads == 0)
     icp_tune_erase(H_l, W_l, n_pairs);
   else
     icp_tune_set(H_l, W_l, n_pairs, threads, blocks_per_pair);
-  if (schedule >= 0) icp_sched_set(H_l, W_l, n_pairs, schedule == 1);
+  if (schedule >= 0) icp_sched_set(H_l, W_l, n_pairs, schedule);
   return RIMG_OK;
 }
 

@@ -23,7 +23,7 @@ struct DevLevel {
 
 DevLevel dev_level(const rimg_sensor* s, int level);
 
-enum KernelId { K_UNPROJECT = 0, K_PYRAMID = 1, K_NORMALS = 2, K_ICP = 3, K_SRC_PYRAMID = 4, K_SOLVE = 5, K_SDF = 6, K_POINTS = 7, K_ICP_ITERS = 8, K_ICP_QUEUE = 9 };
+enum KernelId { K_UNPROJECT = 0, K_PYRAMID = 1, K_NORMALS = 2, K_ICP = 3, K_SRC_PYRAMID = 4, K_SOLVE = 5, K_SDF = 6, K_POINTS = 7, K_ICP_ITERS = 8, K_ICP_QUEUE = 9, K_ICP_CLUSTER = 10 };
 
 // Launch-timing hooks (no-ops unless rimg_profile_begin was called).
 void prof_before(cudaStream_t st, int kernel, int level, int n);
@@ -61,10 +61,13 @@ void icp_grid(int H, int W, int n_pairs, int* bpp, int* rows_per_block, int* thr
 void icp_tune_set(int H, int W, int n_pairs, int threads, int bpp);
 void icp_tune_clear();
 void icp_tune_erase(int H, int W, int n_pairs);
-// The schedule of a level that fits one block (rimg_autotune's choice for
-// (H, W, pairs); default: fused, all iterations in one block per pair).
-void icp_sched_set(int H, int W, int n_pairs, bool fused);
-bool icp_sched_fused(int H, int W, int n_pairs);
+// The schedule of a level (rimg_autotune's choice for (H, W, pairs)): 0 one
+// association launch and one solve launch per iteration (the default for
+// levels that do not fit one block), 1 all iterations in one block per pair
+// (the default where the pair fits one block; taken only there), 2, 4 or 8
+// all iterations on a cluster of that many blocks per pair.
+void icp_sched_set(int H, int W, int n_pairs, int sched);
+int icp_sched(int H, int W, int n_pairs);
 int icp_tune_size();
 // A copy of the whole table (shapes and schedules), put back by
 // icp_tune_restore; icp_tune_free releases the copy.
@@ -79,6 +82,11 @@ cudaError_t launch_solve(int n_pairs, double* sums, double* pose, int* status, c
 constexpr int kIcpItersMaxChunks = 4096;
 bool icp_iters_fits(int H, int W);
 cudaError_t launch_icp_iters(IcpLaunch a, int iters, cudaStream_t st);
+// All iterations of a level with each pair on a thread-block cluster of
+// `cluster` (2, 4 or 8) blocks of 128 threads (no gate, no association
+// output); bit-identical to `cluster` blocks per pair in per-iteration
+// launches.
+cudaError_t launch_icp_cluster(IcpLaunch a, int iters, int cluster, cudaStream_t st);
 
 cudaError_t launch_center(const DevLevel& S, const DevLevel& D, int n_pairs, const float* src, const float* dst,
                           double* T_out, int* status, cudaStream_t st);

@@ -500,7 +500,7 @@ def rimg_profile_end(cap=100000):
 
 
 KERNEL_NAMES = {0: "unproject", 1: "pyramid", 2: "normals", 3: "icp_step", 4: "src_pyramid", 5: "solve", 6: "sdf", 7: "points",
-                8: "icp_iters", 9: "icp_queue"}
+                8: "icp_iters", 9: "icp_queue", 10: "icp_cluster"}
 
 __all__ = [n for n in dir() if n.startswith("rimg_")] + ["Sensor", "Groups", "ProposalNet", "RimgError", "KERNEL_NAMES",
                                                           "RIMG_MAX_LEVELS", "RIMG_FLAG_DEGENERATE", "lib"]

@@ -128,6 +128,21 @@ def test_entry_points_reject_null_and_bad_arguments():
     assert lib.rimg_gn_update(1, fake + 4, fake, None, None) == -1   # sums not 8-byte aligned
 
 
+def test_autotune_set_takes_the_cluster_schedules():
+    """Schedules -1 (leave), 0 (per-iteration launches), 1 (one block per
+    pair), 2, 4 and 8 (clusters of that many blocks per pair); nothing else.
+    The table is host memory: no device is touched."""
+    lib = R.lib()
+    try:
+        for s in (-1, 0, 1, 2, 4, 8):
+            assert lib.rimg_autotune_set(32, 512, 7, 0, 0, s) == 0, s
+        for s in (-2, 3, 5, 6, 7, 9, 16):
+            assert lib.rimg_autotune_set(32, 512, 7, 0, 0, s) == -1, s
+        assert lib.rimg_autotune_set(32, 512, 7, 128, 33, 2) == -1      # blocks per pair above H_l
+    finally:
+        assert lib.rimg_autotune_clear() == 0
+
+
 def test_normals_entry_point_rejects_misaligned_buffers_on_the_host():
     """rimg_normals reads ranges and writes planes 16 bytes at a time: a
     range or plane pointer off a 16-byte boundary is refused before any launch."""

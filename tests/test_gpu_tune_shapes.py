@@ -87,8 +87,9 @@ def test_every_tuner_shape_gives_the_same_sums(R, cfg_name, n):
 
 def test_autotune_set_rejects_bad_arguments(R):
     for args in [(0, 64, 1, 128, 1, -1), (16, 64, 0, 128, 1, -1), (16, 64, 1, 192, 1, -1), (16, 64, 1, 128, 0, -1),
-                 (16, 64, 1, 128, 17, -1), (16, 64, 1, 128, 1, 2), (16, 64, 1, 128, 1, -2)]:
+                 (16, 64, 1, 128, 17, -1), (16, 64, 1, 128, 1, 3), (16, 64, 1, 128, 1, 5), (16, 64, 1, 128, 1, -2)]:
         with pytest.raises(R.RimgError):
             R.rimg_autotune_set(*args)
-    R.rimg_autotune_set(16, 64, 1, 0, 0, 1)
+    for s in (0, 1, 2, 4, 8):
+        R.rimg_autotune_set(16, 64, 1, 0, 0, s)
     R.rimg_autotune_clear()
