@@ -71,8 +71,15 @@ FP32_SUM_REL = 4 * 2.0 ** -24
 
 
 def step_tolerance(cond, step_size, step_tol=STEP_TOL):
-    """Per-step tolerance of the step-arithmetic comparison (rad and m)."""
-    return np.maximum(step_tol, np.asarray(cond) * FP32_SUM_REL * np.asarray(step_size))
+    """Per-step tolerance of the step-arithmetic comparison (rad and m).  A
+    step of size zero (a degenerate system, skipped) has a zero perturbation
+    bound whatever its condition number (a singular system has cond = inf;
+    inf * 0 is taken as 0, not NaN)."""
+    cond = np.asarray(cond, np.float64)
+    size = np.asarray(step_size, np.float64)
+    with np.errstate(invalid="ignore"):
+        bound = np.where(size > 0, cond * FP32_SUM_REL * size, 0.0)
+    return np.maximum(step_tol, bound)
 
 
 def truncated_schedule(iters, k, j):

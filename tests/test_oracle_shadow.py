@@ -101,3 +101,6 @@ def test_step_tolerance_floor_and_scaling():
     big = step_tolerance(1e4, 10.0)
     assert big == pytest.approx(1e4 * FP32_SUM_REL * 10.0)
     np.testing.assert_allclose(step_tolerance([1.0, 1e4], [1e-3, 10.0]), [STEP_TOL, big])
+    # a skipped step (singular system: cond inf, size 0) keeps the floor, not NaN;
+    # a step taken on a singular system is unbounded
+    np.testing.assert_array_equal(step_tolerance([np.inf, np.inf], [0.0, 1.0]), [STEP_TOL, np.inf])
