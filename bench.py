@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true", help="skip the uneven-batch (mixed512) key of the default line")
     ap.add_argument("--no-latency", action="store_true",
                     help="skip the single-pair latency key (latency_1pair) of the default line")
+    ap.add_argument("--no-growth", action="store_true",
+                    help="skip the growth-row keys (sdf, learned) of the default line")
     ap.add_argument("--no-graph", action="store_true",
                     help="time eager rimg_register calls as the headline instead of a CUDA-graph replay of the call")
     ap.add_argument("--no-autotune", action="store_true",
@@ -665,8 +667,39 @@ def run_ours(args):
     if not args.no_latency and world == 1:
         # one pair at a time (an odometry loop's pattern), outside every timed region above
         line["latency_1pair"] = latency_measure(local)
+    if not args.no_growth and world == 1:
+        # the growth rows, each by this script's own workload in a child process (its own CUDA
+        # context and timed region), after everything above
+        line["growth"] = {w: growth_measure(w) for w in ("sdf", "learned")}
     print(json.dumps(line))
     return 0
+
+
+GROWTH_KEYS = {
+    "sdf": ("metric", "value", "unit", "ms_per_step", "roofline", "clocks"),
+    "learned": ("metric", "value", "unit", "plain_pairs_per_s", "plain_success", "learned_success",
+                "speedup_vs_plain", "matched_plain", "gain_vs_matched_plain", "rejected", "clocks"),
+}
+
+
+def growth_measure(workload, timeout_s=600):
+    """`bench.py --workload <workload>` in a child process; the summary of its
+    JSON line (or the reason it gave none)."""
+    cmd = [sys.executable, os.path.abspath(__file__), "--workload", workload, "--steps", "5", "--warmup", "3",
+           "--no-cpu-baseline"]
+    t0 = time.perf_counter()
+    try:
+        r = subprocess.run(cmd, capture_output=True, text=True, timeout=timeout_s)
+    except subprocess.TimeoutExpired:
+        return {"error": f"timed out after {timeout_s} s"}
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    if r.returncode != 0 or not lines:
+        return {"error": f"exit {r.returncode}: {r.stderr.strip().splitlines()[-1:] }"}
+    d = json.loads(lines[-1])
+    out = {k: d[k] for k in GROWTH_KEYS[workload] if k in d}
+    out["command"] = "python bench.py --workload %s --steps 5 --warmup 3 --no-cpu-baseline" % workload
+    out["wall_s"] = time.perf_counter() - t0
+    return out
 
 
 def latency_measure(local, reps=30):
@@ -1017,7 +1050,8 @@ def run_learned(args):
     st_ = train["label_step"]
     tau = (float(np.quantile(st_[:, 0], 0.99)), float(np.quantile(st_[:, 1], 0.99)))
     with ClockSampler(local) as clk:
-        res = Lr.evaluate(R, net, reg, test, [(2, 6, 6, 6), (2, 10, 10, 10)], tau, timing_pairs=4096, log=quiet)
+        res = Lr.evaluate(R, net, reg, test, [(2, 6, 6, 6), (2, 10, 10, 10)], tau, timing_pairs=4096, log=quiet,
+                          plain_schedules=Lr.PLAIN_ABLATION)
     if rank != 0:
         return 0
     best = res["learned"][0]
@@ -1034,6 +1068,8 @@ def run_learned(args):
         "speedup_vs_plain": best["pairs_per_s"] / res["plain"]["pairs_per_s"],
         "learned_2_10_10_10": {"success": res["learned"][1]["judged"]["success"],
                                "pairs_per_s": res["learned"][1]["pairs_per_s"]},
+        # the ablation: the fastest plain schedule (from the identity) that is as accurate
+        "matched_plain": best["matched_plain"], "gain_vs_matched_plain": best["gain_vs_matched"],
         "proposal_median_error": [res["proposal_only"]["median_rot_rad"], res["proposal_only"]["median_trans_m"]],
         "identity_median_error": [res["identity_start"]["median_rot_rad"], res["identity_start"]["median_trans_m"]],
         "clocks": clk.summary(),
