@@ -230,9 +230,10 @@ __device__ __forceinline__ void accumulate_px(float2 (&t)[kPairs], float x, floa
                                               float inv_delta) {
   const float nx = pl.x, ny = pl.y, nz = pl.z;
   const float e = fmaf(nx, x, fmaf(ny, y, fmaf(nz, z, -pl.w)));
-  // a select, not a branch, so that the four pixels of a chunk stay one block
+  // no branch, so that the four pixels of a chunk stay one block; without a
+  // robust kernel inv_delta = 0, q = 0 and w = rsqrt(1) = 1 exactly
   const float q = e * inv_delta;
-  const float w = inv_delta > 0.f ? rsqrtf(fmaf(q, q, 1.f)) : 1.f;
+  const float w = rsqrtf(fmaf(q, q, 1.f));
   const float a0 = fmaf(y, nz, -z * ny), a1 = fmaf(z, nx, -x * nz), a2 = fmaf(x, ny, -y * nx);
   const float2 P1 = f2(a0, a1), P2 = f2(a2, e), N1 = f2(nx, ny);
   const float2 M1 = f2(ny, nx), S2 = f2(e, a2), Z2 = f2(nz, nz);

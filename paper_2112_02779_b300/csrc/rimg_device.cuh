@@ -28,7 +28,10 @@ __device__ __forceinline__ float3 unproject_px(const DevLevel& L, int u, int v, 
 template <bool EXACT = false>
 __device__ __forceinline__ int row_from_sin(const DevLevel& L, float s) {
   int b = __float2int_rd((s - L.s_lo) * L.bin_scale);
-  b = min(max(b, 0), L.n_bins - 1);
+  // clamp into the table; EXACT: one unsigned minimum (a negative bin, s
+  // below the field of view, lands on the last bin -- its row is not used,
+  // the caller's field-of-view test rejects the point)
+  b = EXACT ? (int)min((unsigned)b, (unsigned)(L.n_bins - 1)) : min(max(b, 0), L.n_bins - 1);
   const int4 e = __ldg(L.bins + b);
   if (EXACT || L.bins_exact) return (s > __int_as_float(e.z)) ? e.y : e.x;   // tie rule folded into the boundary
   int j = e.w;
