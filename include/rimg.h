@@ -379,7 +379,9 @@ int rimg_register_groups(int n_groups, const rimg_group* groups, void* workspace
  *    thread-block cluster of 2, 4 or 8 blocks per pair (one launch; the
  *    blocks exchange their sums through distributed shared memory, one
  *    cluster barrier per iteration) -- and records the fastest schedule;
- *  - records the best shape for levels that run as per-iteration launches.
+ *  - for levels that run as per-iteration launches, times the default shape
+ *    and the three fastest shapes of the sweep over whole calls and records
+ *    the fastest (or no entry, where the default wins).
  * The choices go to a process-wide table keyed by (level size, pairs) that
  * later rimg_register / rimg_register_groups calls use.  Last, the whole call
  * is timed with the new table and with the table as rimg_autotune found it

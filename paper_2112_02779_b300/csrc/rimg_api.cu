@@ -6,9 +6,11 @@
 #include <cstdio>
 #include <cstring>
 #include <functional>
+#include <map>
 #include <mutex>
 #include <numeric>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "rimg_internal.h"
@@ -134,9 +136,10 @@ DevLevel dev_level(const rimg_sensor* s, int l) {
   d.s_lo = L.s_lo;
   d.s_hi = L.s_hi;
   d.bin_scale = L.bin_scale;
-  d.w_over_2pi = L.w_over_2pi;
+  d.wf = (float)L.W;
   d.r0 = s->r0;
   d.inv_w2 = 2.0f / (float)L.W;
+  d.col_magic = (float)(1.5 * 8388608.0 / (double)L.W);
   return d;
 }
 
@@ -1236,6 +1239,8 @@ int autotune_impl(int n_groups, const rimg_group* groups, char* ws, cudaStream_t
   int entries = 0;
   std::vector<std::tuple<int, int, int>> done;
   std::vector<std::tuple<int, int, int>> fitting;   // (H_l, W_l, pairs) of levels that fit one block
+  // every shape's standalone time, per (H_l, W_l, pairs)
+  std::map<std::tuple<int, int, int>, std::vector<std::tuple<float, int, int>>> shape_cands;
   for (const Slice& sl : slices) {
     const rimg_group& g = groups[sl.group];
     const int H = g.src->H, W = g.src->W;
@@ -1288,6 +1293,7 @@ int autotune_impl(int n_groups, const rimg_group* groups, char* ws, cudaStream_t
             ms = std::min(ms, t);
           }
           if (ms < best) { best = ms; best_t = T; best_b = bp; }
+          shape_cands[std::make_tuple(Hl, Wl, sl.n)].push_back(std::make_tuple(ms, T, bp));
         }
       }
       icp_tune_set(Hl, Wl, sl.n, best_t, best_b);
@@ -1346,6 +1352,32 @@ int autotune_impl(int n_groups, const rimg_group* groups, char* ws, cudaStream_t
     ++entries;
     // launch shapes stay only for levels that run as per-iteration launches
     if (best_s != 0) {
+      icp_tune_erase(Hl, Wl, n);
+      --entries;
+    }
+  }
+  // Launch shapes of the levels that run as per-iteration launches, chosen in
+  // context: the default shape and the three fastest shapes of the
+  // standalone sweep, each timed over whole calls (the shape fastest alone is
+  // not always the fastest beside the other sub-batches' launches).
+  for (auto& kv : shape_cands) {
+    const int Hl = std::get<0>(kv.first), Wl = std::get<1>(kv.first), n = std::get<2>(kv.first);
+    if (icp_sched(Hl, Wl, n) != 0) continue;
+    std::vector<std::tuple<float, int, int>> v = kv.second;
+    std::sort(v.begin(), v.end());
+    float best = 1e30f, ms = 0.f;
+    int best_t = 0, best_b = 0;    // threads 0: the default shape (no entry)
+    icp_tune_erase(Hl, Wl, n);
+    if ((rc = time_call(&ms))) return rc;
+    best = ms;
+    for (size_t i = 0; i < v.size() && i < 3; ++i) {
+      icp_tune_set(Hl, Wl, n, std::get<1>(v[i]), std::get<2>(v[i]));
+      if ((rc = time_call(&ms))) return rc;
+      if (ms < best) { best = ms; best_t = std::get<1>(v[i]); best_b = std::get<2>(v[i]); }
+    }
+    if (best_t) {
+      icp_tune_set(Hl, Wl, n, best_t, best_b);
+    } else {
       icp_tune_erase(Hl, Wl, n);
       --entries;
     }

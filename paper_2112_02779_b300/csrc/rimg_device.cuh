@@ -45,28 +45,45 @@ __device__ __forceinline__ int row_from_sin(const DevLevel& L, float s) {
   return __ldg(L.rank2row + j);
 }
 
-// atan2(y, x) in (-pi, pi] from an odd polynomial of degree 15 for atan(t)
-// on t in [0, 1] (coefficients fitted here by iteratively re-weighted least
-// squares on Chebyshev nodes, i.e. close to minimax; max error 3.7e-8 rad in
-// exact arithmetic, 1.3e-7 rad evaluated in FP32) and the octant symmetries
-// atan(t) = pi/2 - atan(1/t), atan2(y, -x) = pi - atan2(y, x).
-__device__ __forceinline__ float atan2_poly(float y, float x) {
+// atan2(y, x) / (2 pi), in turns of a full circle, (-1/2, 1/2]: an odd
+// polynomial of degree 15 for atan(t) / (2 pi) on t in [0, 1] and the octant
+// symmetries atan(t) = pi/2 - atan(1/t), atan2(y, -x) = pi - atan2(y, x)
+// (a quarter and a half turn).  The coefficients are those of a fit of
+// atan(t) made here by iteratively re-weighted least squares on Chebyshev
+// nodes (close to minimax; max error 3.7e-8 rad in exact arithmetic), divided
+// by 2 pi and rounded to FP32; evaluated in FP32 the result is within about
+// 3.7e-8 turns (2.3e-7 rad; the spacing of FP32 values near a quarter turn is
+// 3e-8), i.e. 4e-5 columns of a 1024-wide image.  In turns, the column of a
+// W-wide image is the turn count times W, exact for a power-of-two W.
+__device__ __forceinline__ float atan2_turns(float y, float x) {
   const float ax = fabsf(x), ay = fabsf(y);
   const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
   const float t = __fdividef(mn, mx);
   const float t2 = t * t;
-  float p = -0.004054551851790431f;
-  p = fmaf(p, t2, 0.021862905109892965f);
-  p = fmaf(p, t2, -0.05591225506199317f);
-  p = fmaf(p, t2, 0.096421924387434f);
-  p = fmaf(p, t2, -0.13908627803290416f);
-  p = fmaf(p, t2, 0.19946565342346506f);
-  p = fmaf(p, t2, -0.3332986076193729f);
-  p = fmaf(p, t2, 0.999999335574615f);
+  float p = -0.00064530195f;
+  p = fmaf(p, t2, 0.0034795895f);
+  p = fmaf(p, t2, -0.008898712f);
+  p = fmaf(p, t2, 0.015346026f);
+  p = fmaf(p, t2, -0.02213627f);
+  p = fmaf(p, t2, 0.031745944f);
+  p = fmaf(p, t2, -0.053046122f);
+  p = fmaf(p, t2, 0.15915483f);
   float r = p * t;
-  r = (ay > ax) ? 1.57079632679489662f - r : r;
-  r = (x < 0.f) ? 3.14159265358979324f - r : r;
+  r = (ay > ax) ? 0.25f - r : r;
+  r = (x < 0.f) ? 0.5f - r : r;
   return copysignf(r, y);
+}
+
+// round(turns * W) mod W for a power-of-two W = 2^k, by one FP32 addition:
+// `magic` = 1.5 * 2^(23 - k) puts the sum in a binade whose spacing is
+// exactly 1/W, so the addition itself rounds turns to the nearest multiple
+// of 1/W (ties to even, like the conversion of the general form), and the
+// low k bits of the sum's pattern are that multiple's count mod W (the sum is
+// 2^(23 - k) (1 + 2^-1) + j / W, whose pattern ends in 2^22 + j, and 2^22 is
+// a multiple of W).  |turns| <= 1/2, so the sum never leaves the binade; NaN
+// gives column 0, as the conversion does.
+__device__ __forceinline__ int col_from_turns_pow2(float turns, float magic, int W) {
+  return __float_as_int(turns + magic) & (W - 1);
 }
 
 // Column from the continuous estimate u_c: u_c rounded to the nearest
@@ -101,12 +118,18 @@ __device__ __forceinline__ bool project_px(const DevLevel& L, float3 x, int proj
     s = x.z * inv;
     r = n2 * inv;
     v = row_from_sin<FAST>(L, s);
-    float uc = atan2_poly(x.y, x.x) * L.w_over_2pi;
-    if (!FAST && L.has_theta) uc -= __ldg(L.thu + v);
-    u = FAST ? (__float2int_rn(uc) & (L.W - 1)) : wrap_col(uc, L.W);
+    const float turns = atan2_turns(x.y, x.x);
+    if (FAST) {
+      u = col_from_turns_pow2(turns, L.col_magic, L.W);
+    } else {
+      float uc = turns * L.wf;
+      if (L.has_theta) uc -= __ldg(L.thu + v);
+      u = wrap_col(uc, L.W);
+    }
   } else {
     // receiver-offset fixed point on the column angle 2 pi u_c / W
-    float uc = atan2_poly(x.y, x.x) * L.w_over_2pi;
+    float turns = atan2_turns(x.y, x.x);
+    float uc = turns * L.wf;
     s = 0.f;
     r = 0.f;
     v = 0;
@@ -120,10 +143,11 @@ __device__ __forceinline__ bool project_px(const DevLevel& L, float3 x, int proj
       s = x.z * inv;
       r = n2 * inv;
       v = row_from_sin<FAST>(L, s);
-      uc = atan2_poly(yp, xp) * L.w_over_2pi;
+      turns = atan2_turns(yp, xp);
+      uc = turns * L.wf;
       if (!FAST && L.has_theta) uc -= __ldg(L.thu + v);
     }
-    u = FAST ? (__float2int_rn(uc) & (L.W - 1)) : wrap_col(uc, L.W);
+    u = FAST ? col_from_turns_pow2(turns, L.col_magic, L.W) : wrap_col(uc, L.W);
   }
   return (s >= L.s_lo) && (s <= L.s_hi);   // false for NaN
 }

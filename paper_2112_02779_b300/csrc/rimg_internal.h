@@ -18,7 +18,8 @@ struct DevLevel {
   const float* bnd;       // [H-1]
   const int4* bins;       // [n_bins] (row_lo, row_hi, boundary bits, rank at lower edge)
   int H, W, n_bins, tie_up, bins_exact, has_theta;
-  float s_lo, s_hi, bin_scale, w_over_2pi, r0, inv_w2;   // inv_w2 = 2 / W
+  float s_lo, s_hi, bin_scale, wf, r0, inv_w2;   // wf = W, inv_w2 = 2 / W
+  float col_magic;        // 1.5 * 2^23 / W (the column rounding of a power-of-two W)
 };
 
 DevLevel dev_level(const rimg_sensor* s, int level);
