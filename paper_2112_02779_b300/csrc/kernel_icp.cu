@@ -370,8 +370,11 @@ __device__ __forceinline__ float warp_scatter_sum(const float2 (&t)[kPairs], int
 // the pose in sm.T4, whose row table (icp_row_table) the caller has filled.
 // On return (after a block barrier) sm.red[w][l] holds warp w's component l
 // of the 29 sums (lane order, see kFlat).
-// ROWSTRIDE: the thread stride is a whole number of rows (chunks per row
-// divide THREADS), so a cursor advances by rows only.  FAST: the target
+// ROWSTRIDE 1: the thread stride is a whole number of rows (chunks per row
+// divide THREADS), so a cursor advances by rows only; ROWSTRIDE 2: the
+// stride is half a row (2 THREADS chunks per row), so a thread's chunks j
+// sit at row v_begin + j / 2, column chunk tid + (j odd) THREADS -- the
+// two-slot ring's slot is the parity, and no cursor is kept.  FAST: the target
 // level's inverse table is exact, it has no azimuth offsets and its width is
 // a power of two (the projection has no branch).
 // The first two source-range fetches of icp_block_terms (chunks tid and
@@ -398,7 +401,7 @@ __device__ __forceinline__ void icp_prefetch(const IcpLaunch& a, IcpSmem<THREADS
   cp_async_commit();
 }
 
-template <bool R0, bool GATE, bool ASSOC, bool KAHAN, int THREADS, bool ROWSTRIDE = false, bool FAST = false>
+template <bool R0, bool GATE, bool ASSOC, bool KAHAN, int THREADS, int ROWSTRIDE = 0, bool FAST = false>
 __device__ __forceinline__ void icp_block_terms(const IcpLaunch& a, IcpSmem<THREADS>& sm, int pair, int v_begin,
                                                 int v_end, bool prefetched = false) {
   const int tid = threadIdx.x;
@@ -434,8 +437,10 @@ __device__ __forceinline__ void icp_block_terms(const IcpLaunch& a, IcpSmem<THRE
     int v, cu;
   };
   const Cursor start{v_begin + tid / cpr, tid - (tid / cpr) * cpr};
+  constexpr bool HALF = ROWSTRIDE == 2;
+  static_assert(!HALF || (!GATE && !ASSOC), "the half-row form has no association output and no gate");
   auto advance = [&](Cursor& k) {
-    if (ROWSTRIDE) {
+    if (ROWSTRIDE == 1) {
       k.v += dv;
     } else {
       k.cu += dcu;
@@ -444,10 +449,16 @@ __device__ __forceinline__ void icp_block_terms(const IcpLaunch& a, IcpSmem<THRE
     }
   };
   Cursor cf = start, ci = start, cc = start;   // fetch, issue, consume
+  int vrow = v_begin;   // HALF: the row of the current even / odd step pair
 
+  // the source ranges of the chunk two steps ahead (same slot)
   auto fetch_src = [&](int slot) {
-    cp_async16_zfill(&sm.src[slot][tid], src + (long long)cf.v * W + (cf.cu << 2), true);
-    advance(cf);
+    if (HALF) {
+      cp_async16_zfill(&sm.src[slot][tid], src + (long long)(vrow + 1) * W + ((tid + slot * THREADS) << 2), true);
+    } else {
+      cp_async16_zfill(&sm.src[slot][tid], src + (long long)cf.v * W + (cf.cu << 2), true);
+      advance(cf);
+    }
   };
 
   struct Pts {
@@ -459,8 +470,15 @@ __device__ __forceinline__ void icp_block_terms(const IcpLaunch& a, IcpSmem<THRE
   // gathers of its target planes (zero-filled when the pixel has no
   // association).
   auto issue = [&](int slot, Pts& P) {
-    const int v = ci.v, u0 = ci.cu << 2;
-    advance(ci);
+    int v, u0;
+    if (HALF) {
+      v = vrow;
+      u0 = (tid + slot * THREADS) << 2;
+    } else {
+      v = ci.v;
+      u0 = ci.cu << 2;
+      advance(ci);
+    }
     const float4 r4 = sm.src[slot][tid];
     const float rr[4] = {r4.x, r4.y, r4.z, r4.w};
     const float4 cc4 = __ldg(reinterpret_cast<const float4*>(S.cos_u + u0));
@@ -494,7 +512,7 @@ __device__ __forceinline__ void icp_block_terms(const IcpLaunch& a, IcpSmem<THRE
       P.y[q] = Y;
       P.z[q] = Z;
       P.idx[q] = ok ? idx : -1;    // read by the gate and the association output only
-      gidx[q] = ok ? idx : 0;
+      gidx[q] = idx;               // a valid index whatever ok (project_px), read only when ok
       gok[q] = ok;
     }
     // The gathers after all four projections: each copy is an asm statement
@@ -558,11 +576,16 @@ __device__ __forceinline__ void icp_block_terms(const IcpLaunch& a, IcpSmem<THRE
   static_assert(kRing == 2, "the pipeline below is written for a two-slot ring");
   Pts P0, P1;
   if (prefetched) {          // chunks 0 and 1 were fetched by icp_prefetch
-    if (nmine > 0) advance(cf);
-    if (nmine > 1) advance(cf);
+    if (!HALF && nmine > 0) advance(cf);
+    if (!HALF && nmine > 1) advance(cf);
   } else {
-    if (nmine > 0) fetch_src(0);
-    if (nmine > 1) fetch_src(1);
+    if (HALF) {
+      if (nmine > 0) cp_async16_zfill(&sm.src[0][tid], src + (long long)v_begin * W + (tid << 2), true);
+      if (nmine > 1) cp_async16_zfill(&sm.src[1][tid], src + (long long)v_begin * W + ((tid + THREADS) << 2), true);
+    } else {
+      if (nmine > 0) fetch_src(0);
+      if (nmine > 1) fetch_src(1);
+    }
     cp_async_commit();
   }
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
@@ -584,6 +607,7 @@ __device__ __forceinline__ void icp_block_terms(const IcpLaunch& a, IcpSmem<THRE
       issue(1, P1);
       if (i + 2 < nmine) fetch_src(1);
     }
+    if (HALF) ++vrow;
     cp_async_commit();
     asm volatile("cp.async.wait_group 1;\n" ::: "memory");
     if (i - 1 < nmine) consume(0, P0);
@@ -612,7 +636,7 @@ __device__ __forceinline__ float block_total(const IcpSmem<THREADS>& sm, int tid
   return acc;
 }
 
-template <bool R0, bool GATE, bool ASSOC, bool KAHAN, int THREADS, bool ROWSTRIDE = false, bool FAST = false>
+template <bool R0, bool GATE, bool ASSOC, bool KAHAN, int THREADS, int ROWSTRIDE = 0, bool FAST = false>
 __global__ void __launch_bounds__(THREADS, RIMG_ICP_THREADS_PER_SM / THREADS) k_icp(IcpLaunch a) {
   extern __shared__ float4 smem_raw[];
   IcpSmem<THREADS>& sm = *reinterpret_cast<IcpSmem<THREADS>*>(smem_raw);
@@ -706,7 +730,7 @@ __global__ void __launch_bounds__(128) k_solve(int n_pairs, double* sums, double
 // level whose pair fits one block collapse into one.  Same arithmetic as
 // k_icp with one block per pair followed by k_solve.  The pair's final sums
 // and step record are left in a.sums (as after the last k_solve).
-template <bool R0, bool GATE, bool KAHAN, int THREADS, bool ROWSTRIDE = false, bool FAST = false>
+template <bool R0, bool GATE, bool KAHAN, int THREADS, int ROWSTRIDE = 0, bool FAST = false>
 __global__ void __launch_bounds__(THREADS, RIMG_ICP_THREADS_PER_SM / THREADS) k_icp_iters(IcpLaunch a, int iters) {
   extern __shared__ float4 smem_raw[];
   IcpSmem<THREADS>& sm = *reinterpret_cast<IcpSmem<THREADS>*>(smem_raw);
@@ -762,7 +786,7 @@ __global__ void __launch_bounds__(THREADS, RIMG_ICP_THREADS_PER_SM / THREADS) k_
 // cluster runs the same number of iterations, so every barrier completes.
 namespace cg = cooperative_groups;
 
-template <bool R0, bool KAHAN, int THREADS, bool ROWSTRIDE, bool FAST, int C>
+template <bool R0, bool KAHAN, int THREADS, int ROWSTRIDE, bool FAST, int C>
 __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(THREADS, RIMG_ICP_THREADS_PER_SM / THREADS)
     k_icp_cluster(IcpLaunch a, int iters) {
   extern __shared__ float4 smem_raw[];
@@ -1098,13 +1122,16 @@ inline bool row_stride(const IcpLaunch& a, int T) {
   return cpr > 0 && cpr <= T && T % cpr == 0;
 }
 
+// Whether a thread stride of T chunks is half a row of the level.
+inline bool half_row(const IcpLaunch& a, int T) { return (a.src.W >> 2) == 2 * T; }
+
 // Whether the target level's projection needs neither the boundary walk nor
 // the azimuth offsets, and its columns wrap by a mask (power-of-two width).
 inline bool fast_projection(const IcpLaunch& a) {
   return a.dst.bins_exact && !a.dst.has_theta && a.dst.W > 0 && (a.dst.W & (a.dst.W - 1)) == 0;
 }
 
-template <bool R0, bool GATE, bool ASSOC, bool KAHAN, int T, bool ROWSTRIDE, bool FAST = false>
+template <bool R0, bool GATE, bool ASSOC, bool KAHAN, int T, int ROWSTRIDE, bool FAST = false>
 cudaError_t launch_icp_ts(const IcpLaunch& a, long long blocks, cudaStream_t st) {
   const size_t bytes = icp_smem_bytes<T>(a.rows_per_block);
   static bool configured = false;   // per instantiation; the attribute is per function
@@ -1126,12 +1153,16 @@ cudaError_t launch_icp_t(const IcpLaunch& a, long long blocks, cudaStream_t st) 
   if constexpr (!GATE && !ASSOC) {
     const bool fast = fast_projection(a);
     if (row_stride(a, T)) {
-      if (fast) return launch_icp_ts<R0, GATE, ASSOC, KAHAN, T, true, true>(a, blocks, st);
-      return launch_icp_ts<R0, GATE, ASSOC, KAHAN, T, true>(a, blocks, st);
+      if (fast) return launch_icp_ts<R0, GATE, ASSOC, KAHAN, T, 1, true>(a, blocks, st);
+      return launch_icp_ts<R0, GATE, ASSOC, KAHAN, T, 1>(a, blocks, st);
     }
-    if (fast) return launch_icp_ts<R0, GATE, ASSOC, KAHAN, T, false, true>(a, blocks, st);
+    if (half_row(a, T)) {
+      if (fast) return launch_icp_ts<R0, GATE, ASSOC, KAHAN, T, 2, true>(a, blocks, st);
+      return launch_icp_ts<R0, GATE, ASSOC, KAHAN, T, 2>(a, blocks, st);
+    }
+    if (fast) return launch_icp_ts<R0, GATE, ASSOC, KAHAN, T, 0, true>(a, blocks, st);
   }
-  return launch_icp_ts<R0, GATE, ASSOC, KAHAN, T, false>(a, blocks, st);
+  return launch_icp_ts<R0, GATE, ASSOC, KAHAN, T, 0>(a, blocks, st);
 }
 
 template <bool R0, bool GATE, bool ASSOC, bool KAHAN>
@@ -1140,7 +1171,7 @@ cudaError_t launch_icp_k(const IcpLaunch& a, long long blocks, cudaStream_t st) 
                           : launch_icp_t<R0, GATE, ASSOC, KAHAN, 256>(a, blocks, st);
 }
 
-template <bool R0, bool GATE, bool KAHAN, int T, bool ROWSTRIDE, bool FAST = false>
+template <bool R0, bool GATE, bool KAHAN, int T, int ROWSTRIDE, bool FAST = false>
 cudaError_t launch_icp_iters_ts(const IcpLaunch& a, int iters, cudaStream_t st) {
   const size_t bytes = icp_smem_bytes<T>(a.src.H);
   static bool configured = false;
@@ -1173,7 +1204,7 @@ cudaError_t launch_icp_iters_k(const IcpLaunch& a, int iters, cudaStream_t st) {
 
 bool icp_iters_fits(int H, int W) { return H <= kMaxBlockRows && (long long)H * (W / 4) <= kIcpItersMaxChunks; }
 
-template <bool R0, bool KAHAN, bool ROWSTRIDE, bool FAST, int C>
+template <bool R0, bool KAHAN, int ROWSTRIDE, bool FAST, int C>
 cudaError_t launch_icp_cluster_ts(const IcpLaunch& a, int iters, cudaStream_t st) {
   constexpr int T = 128;
   const size_t bytes = icp_smem_bytes<T>(a.rows_per_block);
@@ -1193,10 +1224,13 @@ template <bool R0, bool KAHAN, int C>
 cudaError_t launch_icp_cluster_c(const IcpLaunch& a, int iters, cudaStream_t st) {
   const bool fast = fast_projection(a);
   if (row_stride(a, 128))
-    return fast ? launch_icp_cluster_ts<R0, KAHAN, true, true, C>(a, iters, st)
-                : launch_icp_cluster_ts<R0, KAHAN, true, false, C>(a, iters, st);
-  return fast ? launch_icp_cluster_ts<R0, KAHAN, false, true, C>(a, iters, st)
-              : launch_icp_cluster_ts<R0, KAHAN, false, false, C>(a, iters, st);
+    return fast ? launch_icp_cluster_ts<R0, KAHAN, 1, true, C>(a, iters, st)
+                : launch_icp_cluster_ts<R0, KAHAN, 1, false, C>(a, iters, st);
+  if (half_row(a, 128))
+    return fast ? launch_icp_cluster_ts<R0, KAHAN, 2, true, C>(a, iters, st)
+                : launch_icp_cluster_ts<R0, KAHAN, 2, false, C>(a, iters, st);
+  return fast ? launch_icp_cluster_ts<R0, KAHAN, 0, true, C>(a, iters, st)
+              : launch_icp_cluster_ts<R0, KAHAN, 0, false, C>(a, iters, st);
 }
 
 template <int C>
