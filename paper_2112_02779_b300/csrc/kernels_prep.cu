@@ -272,7 +272,10 @@ __global__ void __launch_bounds__(NT_X* NT_Y) k_normals_pca(DevLevel L, int leve
 // (the same operations in the same order).
 constexpr int NC_LANES_PX = 4;
 constexpr int NC_W = 32 * NC_LANES_PX;   // strip width in pixels
-constexpr int NC_ROWS = 16;              // output rows per strip
+#ifndef RIMG_NC_ROWS
+#define RIMG_NC_ROWS 8
+#endif
+constexpr int NC_ROWS = RIMG_NC_ROWS;    // output rows per strip
 constexpr int NC_WARPS = 4;              // warps per block
 
 // Unprojection (Eq. 1-2) of one pixel from its row entry and column cos/sin;

@@ -133,11 +133,11 @@ def test_normals_parity(R, name, levels):
     _check_normals(R, s, sens, imgs, levels)
 
 
-@pytest.mark.parametrize("H,W,levels", [(8, 136, 1), (12, 64, 2), (24, 1152, 3), (16, 4, 1)])
+@pytest.mark.parametrize("H,W,levels", [(8, 136, 1), (12, 64, 2), (24, 1152, 3), (16, 4, 1), (20, 136, 2)])
 def test_normals_parity_strip_edges(R, H, W, levels):
     """Widths that end inside a 128-column strip (136, 64, 4: the wrap lands in
     a lane of the same warp), a width of nine strips, and heights that end
-    inside a 16-row strip."""
+    inside an 8-row strip (12, 20) or on a strip boundary (8, 16, 24)."""
     from synth import Sensor, outdoor_scene, raycast, uniform_phi
     rng = np.random.default_rng(H * 1000 + W)
     s = Sensor(H, W, uniform_phi(H, 8.0, -20.0), rng.uniform(-0.01, 0.01, H), 0.04)
