@@ -85,7 +85,7 @@ typedef struct rimg_sensor {
 
 /* Method parameters.  Defaults (rimg_default_params): huber_delta 0.5 m (the
  * outdoor kernel size of Section 6.1), no distance gate, normal_rel_jump 0.1,
- * proj_iters 3, kahan 1, streams 4.  Pairs are independent: each sub-batch of
+ * proj_iters 3, kahan 1, streams 2.  Pairs are independent: each sub-batch of
  * at least 32 pairs runs on its own internal stream forked from and joined
  * back into the caller's stream, and `streams` changes results only through
  * the FP32 summation order (a small sub-batch may split each pair over more

@@ -603,7 +603,7 @@ int rimg_default_params(rimg_params* p) {
   p->normal_rel_jump = 0.1f;
   p->proj_iters = 3;
   p->kahan = 1;
-  p->streams = 4;
+  p->streams = 2;
   p->normal_method = 0;
   return RIMG_OK;
 }

@@ -66,7 +66,7 @@ int main(void) {
 def test_default_params_and_status_strings():
     p = R.rimg_default_params()
     assert p.huber_delta == pytest.approx(0.5) and p.max_corr_dist == 0.0
-    assert p.normal_rel_jump == pytest.approx(0.1) and p.proj_iters == 3 and p.kahan == 1 and p.streams == 4
+    assert p.normal_rel_jump == pytest.approx(0.1) and p.proj_iters == 3 and p.kahan == 1 and p.streams == 2
     for code in _abi.STATUS_NAMES:
         assert R.rimg_status_string(code)
     assert R.rimg_status_string(12345) == "unknown status"

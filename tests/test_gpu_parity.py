@@ -519,15 +519,15 @@ def test_register_sub_batch_streams_agree(R):
     cfg = CONFIGS["pair32x512"]
     s = cfg.sensor()
     sens = gpu_sensor(R, s, 3)
-    n = 96
+    n = 128
     src, dst, _ = make_pairs(cfg, range(8))
-    src, dst = np.tile(src, (12, 1, 1)), np.tile(dst, (12, 1, 1))
+    src, dst = np.tile(src, (16, 1, 1)), np.tile(dst, (16, 1, 1))
     T0 = np.tile(np.eye(4), (n, 1, 1))
     out = {}
-    for streams in (1, 2, 3):
+    for streams in (1, 2, 3, 4):
         params = R.rimg_default_params(huber_delta=cfg.huber_delta, streams=streams)
         out[streams], _ = gpu_register(R, torch, sens, src, dst, T0, 3, cfg.iters, params)
-    for streams in (2, 3):
+    for streams in (2, 3, 4):
         for i in range(n):
             eR, et = O.pose_error(out[streams][i], out[1][i])
             assert eR <= 1e-4 and et <= 1e-4
