@@ -330,7 +330,7 @@ __device__ __forceinline__ void icp_row_table(const DevLevel& S, IcpSmem<THREADS
 
 // Chunks summed plainly per thread between two compensated warp steps.
 #ifndef RIMG_WARP_FLUSH
-#define RIMG_WARP_FLUSH 32
+#define RIMG_WARP_FLUSH 16
 #endif
 constexpr int kWarpFlush = RIMG_WARP_FLUSH;
 static_assert(kWarpFlush >= 1, "at least one chunk between warp steps");
